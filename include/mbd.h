@@ -1,0 +1,182 @@
+/*
+ * mbd.h - C ABI of the GB300 SPME stochastic-Lanczos MBD library.
+ *
+ * Method: arXiv 2307.02278 (Poier, Lagardere, Piquemal), "Smooth Particle Mesh
+ * Ewald-integrated stochastic Lanczos Many-body Dispersion algorithm".
+ *
+ *   E_MBD = (1/2) Tr sqrt(C) - (3/2) sum_i w_i                       (Eq. plasmonic2)
+ *   C     = Omega + Diag(g) T'^pbc Diag(g),  Omega = (+)_i w_i^2 I_3,
+ *           g = (+)_i w_i sqrt(alpha_i) 1_3                          (Eqs. ccd, gvec, lk3)
+ *   T'^pbc d = E^dir + E^rec + E^self by Ewald summation, tin-foil boundary,
+ *           with E^rec from SPME                                      (Eqs. ewalddip, fld_ewald,
+ *                                                                      fld_ewald1, spme, dipolarr)
+ *   Tr sqrt(C) ~ (3N/R) sum_l sum_k U_1k^2 sqrt(theta_k) over R Rademacher
+ *           probes and an m-step Lanczos recurrence per probe        (Eqs. hutch, dds, recurs2,
+ *                                                                      sl4; Algorithms 1 and 2)
+ *
+ * Units: atomic units throughout (bohr, hartree, bohr^3).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an mbd_status; nothing aborts or throws across the ABI.
+ *     Output buffers are left untouched when a call fails before its GPU work
+ *     starts (argument errors); after a CUDA error their contents are undefined.
+ *   - Host pointers are read during the call only; the library keeps copies.
+ *     Device pointers ("_dev") are borrowed for the duration of the call only
+ *     and must be device memory of the current CUDA device.
+ *   - All GPU work of a system is enqueued on the stream given at creation;
+ *     every call returns after that work has finished (it synchronises the
+ *     stream), so host outputs are valid on return.
+ *   - A system handle is not thread-safe: one handle per host thread/stream.
+ *   - Probe rule (part of the ABI, so that any implementation draws the same
+ *     probes): u_{l,i} = +1 when the top bit of SplitMix64(seed + (l << 32) + i)
+ *     is 0, else -1; v_l = u_l / sqrt(3N) (Eq. dds).  SplitMix64(x) is the first
+ *     output of Steele, Lea & Flood's SplitMix64 generator started at state x.
+ *   - The library sizes its device memory itself (cudaMalloc), growing it on
+ *     demand; MBD_ERR_OOM is returned when an allocation fails.
+ */
+#ifndef MBD_H
+#define MBD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MBD_OK = 0,
+    MBD_ERR_INVALID_ARG = 1,            /* a null pointer, a size or parameter out of range */
+    MBD_ERR_OOM = 2,                    /* a device or pinned-host allocation failed */
+    MBD_ERR_CUDA = 3,                   /* a CUDA runtime call or kernel launch failed */
+    MBD_ERR_NOT_POSITIVE_DEFINITE = 4,  /* a Ritz value of C was <= 0 (polarisation catastrophe) */
+    MBD_ERR_NONFINITE = 5,              /* a NaN or Inf appeared in a result */
+    MBD_ERR_TIMEOUT = 6,                /* a bounded device-side wait ran out */
+    MBD_ERR_UNSUPPORTED = 7,            /* valid request this build does not support */
+    MBD_ERR_NO_DEVICE = 8               /* no CUDA device is visible */
+} mbd_status;
+
+/* Arithmetic of the operator C (spreading, FFT, influence function, gather,
+ * real-space field).  The Lanczos vectors, dot products, the tridiagonal
+ * eigensolve and the trace sum are always FP64. */
+enum { MBD_FP64 = 0, MBD_MIXED = 1 /* FP32 operator, FP64 Lanczos */ };
+
+/* Field terms for mbd_field (bit mask). */
+enum { MBD_TERM_REAL = 1, MBD_TERM_RECIP = 2, MBD_TERM_SELF = 4, MBD_TERM_ALL = 7 };
+
+typedef struct mbd_system mbd_system;   /* opaque, owned by the library */
+
+/* One periodic system (Eq. ham parameters, Ewald/SPME settings).
+ * damping: T'_ij = s(R_ij) T_ij with the Fermi form
+ *   s(r) = 1 / (1 + exp(-damp_d (r / (damp_beta (Rvdw_i + Rvdw_j)) - 1)))
+ * (the paper defers the explicit damping to its earlier SL-MBD work).
+ * Real space: the erfc-screened field is summed over image pairs with
+ * |r| < r_cut and the damping correction -(1-s) T over |r| < damp_cut
+ * (Eq. fld_ewald); damp_cut <= 0 means damp_cut = r_cut. */
+typedef struct {
+    int32_t n_atoms;          /* N >= 1 */
+    double cell[9];           /* rows a1, a2, a3 (bohr), right-handed (det > 0) */
+    const double *pos;        /* host [N][3] Cartesian (bohr); wrapped into the cell */
+    const double *alpha;      /* host [N] static polarisability (bohr^3), > 0 */
+    const double *omega;      /* host [N] characteristic frequency (Ha), > 0 */
+    const double *r_vdw;      /* host [N] vdW radius (bohr), > 0 */
+    double damp_beta;         /* Fermi range-separation parameter, > 0 */
+    double damp_d;            /* Fermi steepness, > 0 */
+    double ewald_beta;        /* Ewald splitting parameter (bohr^-1), > 0 */
+    double r_cut;             /* real-space cutoff (bohr), > 0 */
+    double damp_cut;          /* damping-correction cutoff (bohr); <= 0: = r_cut */
+    int32_t mesh[3];          /* K_alpha: products of 2, 3, 5 only; 2p <= K_alpha <= 1000 */
+    int32_t spline_order;     /* p: even, 4 <= p <= 10 */
+    int32_t precision;        /* MBD_FP64 or MBD_MIXED */
+} mbd_system_desc;
+
+/* Create a system: validate, upload, build the neighbour list, spline
+ * stencils, the influence function and the FFT tables (Algorithm 1, grid
+ * allocation and neighbour list).  cuda_stream: a cudaStream_t or NULL for the
+ * legacy default stream.  *out receives the handle on MBD_OK. */
+mbd_status mbd_create_system(const mbd_system_desc *desc, void *cuda_stream, mbd_system **out);
+
+/* Release all device and host memory of a system (NULL is ignored). */
+void mbd_destroy_system(mbd_system *sys);
+
+/* New positions (host [N][3], bohr) for the same atoms and cell; rebuilds the
+ * neighbour list and spline stencils. */
+mbd_status mbd_update_positions(mbd_system *sys, const double *pos);
+
+/* y = C x for a block of vectors (Eqs. ccd, lk3): x_dev, y_dev are device
+ * FP64 arrays of layout [nvec][N][3], nvec >= 1; y_dev may not alias x_dev. */
+mbd_status mbd_apply_C(mbd_system *sys, int32_t nvec, const double *x_dev, double *y_dev);
+
+/* Stochastic Lanczos MBD energy (Algorithm 1 with Algorithm 2 per step).
+ * n_probes R >= 1, n_steps m in [1, 128] (m = size of the tridiagonal Delta).
+ * Outputs (host; energy required, the rest may be NULL):
+ *   energy    E_MBD (Ha)
+ *   trace     the estimate of Tr sqrt(C)
+ *   q_host    [R] per-probe quadrature v_l^T sqrt(C) v_l
+ *   ab_host   [R][2][m]: Delta's diagonal a_1..a_m, then the couplings
+ *             b_2..b_m followed by a 0 (b after a breakdown is 0)
+ * Returns MBD_ERR_NOT_POSITIVE_DEFINITE if a Ritz value is <= 0. */
+mbd_status mbd_lanczos_energy(mbd_system *sys, int32_t n_probes, int32_t n_steps, uint64_t seed,
+                              double *energy, double *trace, double *q_host, double *ab_host);
+
+/* Energy and forces F = -dE/dR (Ha/bohr).  The paper computes energies only
+ * and names gradients as future work (Conclusions); the estimator used here is
+ * dE/dR ~ (1/4)(3N/R) sum_l (g.w_l)^T (dT'/dR) (g.v_l) with w_l = C^{-1/2} v_l
+ * from the Lanczos basis of probe l, on the same probes as the energy.
+ * forces_dev: device FP64 [N][3].  Other arguments as mbd_lanczos_energy. */
+mbd_status mbd_energy_forces(mbd_system *sys, int32_t n_probes, int32_t n_steps, uint64_t seed,
+                             double *energy, double *forces_dev);
+
+/* ---- stage-level entry points (per-stage checks and users of single stages) ---- */
+
+/* The normalised probes v_l (l = first..first+R-1) of the probe rule above,
+ * device FP64 [R][dim]. */
+mbd_status mbd_generate_probes(uint64_t seed, int32_t first, int32_t n_probes, int32_t dim,
+                               double *v_dev);
+
+/* Generalised field E = T'^pbc d restricted to the terms in `terms`
+ * (MBD_TERM_*; Eq. ewalddip): d_dev, e_dev device FP64 [nvec][N][3]. */
+mbd_status mbd_field(mbd_system *sys, int32_t nvec, const double *d_dev, double *e_dev, int32_t terms);
+
+/* SPME dipole array D(k) = sum_j d_j . grad W_j(k) (Eq. dipolarr): d_dev device
+ * FP64 [nvec][N][3] -> mesh_dev device FP64 [nvec][K1][K2][K3]. */
+mbd_status mbd_spread(mbd_system *sys, int32_t nvec, const double *d_dev, double *mesh_dev);
+
+/* FFT convolution phi = F^-1[G F[D]] with the system's influence function
+ * (Eq. spme): device FP64 [nvec][K1][K2][K3] in and out (may alias). */
+mbd_status mbd_convolve(mbd_system *sys, int32_t nvec, const double *mesh_in_dev, double *mesh_out_dev);
+
+/* Gauss quadrature of a batch of tridiagonals (Eqs. tridiag2, sl3): host
+ * a [R][m], b [R][m] (b[l][k] couples k and k+1; the entries from the first
+ * zero on are ignored), q [R] out. */
+mbd_status mbd_tridiag_quadrature(int32_t n_probes, int32_t n_steps, const double *a_host,
+                                  const double *b_host, double *q_host);
+
+/* The Lanczos layer alone: the same recurrence, quadrature and estimator as
+ * mbd_lanczos_energy, driven by a dense symmetric FP64 matrix C_dev [dim][dim]
+ * (device).  energy = (1/2) trace - 1.5 * omega_sum. */
+mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double omega_sum,
+                                    int32_t n_probes, int32_t n_steps, uint64_t seed,
+                                    double *energy, double *q_host, double *ab_host);
+
+/* Introspection: number of atoms, mesh, neighbour-pair count and the byte
+ * sizes of the device arrays in use (for measurement). */
+typedef struct {
+    int32_t n_atoms;
+    int32_t mesh[3];
+    int64_t n_pairs;          /* directed real-space pairs (i, j, image) */
+    int64_t device_bytes;     /* device memory held by the system */
+    int32_t precision;
+} mbd_info;
+mbd_status mbd_get_info(const mbd_system *sys, mbd_info *info);
+
+/* Human-readable name of a status code (static storage). */
+const char *mbd_status_string(mbd_status status);
+
+/* Last CUDA error text seen by the library in this thread ("" if none). */
+const char *mbd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBD_H */

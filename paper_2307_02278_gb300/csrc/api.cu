@@ -1,0 +1,833 @@
+// C ABI of libmbd: validation, the per-system setup (neighbour list, spread
+// bins, B-spline moduli, FFT plans) and the orchestration of the per-step
+// kernels for every entry point declared in include/mbd.h.
+#include "mbd_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace mbd {
+
+thread_local std::string g_last_error;
+
+void set_last_error(const char *where, cudaError_t e) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+}
+
+mbd_status DevBuf::ensure(size_t n) {
+    if (ptr != nullptr && n <= bytes) return MBD_OK;
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        set_last_error("cudaMalloc", e);
+        cudaGetLastError();
+        return MBD_ERR_OOM;
+    }
+    bytes = n;
+    return MBD_OK;
+}
+
+void DevBuf::release() {
+    if (ptr != nullptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+// gscale kernels live in kernels_lanczos.cu
+template <class T> mbd_status launch_gscale(const double *x, const double *g, T *d, int rows, int ld, cudaStream_t st);
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+template <class T> PrecData<T> &prec(mbd_system *s);
+template <> PrecData<double> &prec<double>(mbd_system *s) { return s->f64; }
+template <> PrecData<float> &prec<float>(mbd_system *s) { return s->f32; }
+
+bool finite_all(const double *x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+// Radices 8, 4, 2, 3, 5 (in that order of preference); false if K has another factor.
+bool factor_mesh(int K, FFTDim &f) {
+    f.K = K;
+    f.nst = 0;
+    int k = K;
+    const int order[5] = {8, 4, 2, 3, 5};
+    for (int r : order) {
+        while (k % r == 0) {
+            if (f.nst >= kMaxRadixStages) return false;
+            f.radix[f.nst++] = r;
+            k /= r;
+        }
+    }
+    for (int i = f.nst; i < kMaxRadixStages; ++i) f.radix[i] = 1;
+    return k == 1;
+}
+
+mbd_status validate(const mbd_system_desc *d) {
+    if (d == nullptr) return MBD_ERR_INVALID_ARG;
+    if (d->n_atoms < 1 || d->n_atoms > (1 << 24)) return MBD_ERR_INVALID_ARG;
+    if (!d->pos || !d->alpha || !d->omega || !d->r_vdw) return MBD_ERR_INVALID_ARG;
+    if (!finite_all(d->cell, 9)) return MBD_ERR_INVALID_ARG;
+    const double *c = d->cell;
+    const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
+                       c[2] * (c[3] * c[7] - c[4] * c[6]);
+    if (!(det > 0.0)) return MBD_ERR_INVALID_ARG;
+    const size_t n = (size_t)d->n_atoms;
+    if (!finite_all(d->pos, 3 * n)) return MBD_ERR_INVALID_ARG;
+    for (size_t i = 0; i < n; ++i) {
+        if (!(d->alpha[i] > 0.0) || !(d->omega[i] > 0.0) || !(d->r_vdw[i] > 0.0)) return MBD_ERR_INVALID_ARG;
+        if (!std::isfinite(d->alpha[i]) || !std::isfinite(d->omega[i]) || !std::isfinite(d->r_vdw[i]))
+            return MBD_ERR_INVALID_ARG;
+    }
+    if (!(d->damp_beta > 0.0) || !(d->damp_d > 0.0) || !(d->ewald_beta > 0.0) || !(d->r_cut > 0.0))
+        return MBD_ERR_INVALID_ARG;
+    if (!std::isfinite(d->damp_beta) || !std::isfinite(d->damp_d) || !std::isfinite(d->ewald_beta) ||
+        !std::isfinite(d->r_cut) || !std::isfinite(d->damp_cut))
+        return MBD_ERR_INVALID_ARG;
+    const int p = d->spline_order;
+    if (p < 4 || p > kMaxOrder || (p & 1)) return MBD_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+        FFTDim f;
+        if (d->mesh[a] < 2 * p || d->mesh[a] > 1000 || !factor_mesh(d->mesh[a], f)) return MBD_ERR_INVALID_ARG;
+    }
+    if (d->precision != MBD_FP64 && d->precision != MBD_MIXED) return MBD_ERR_INVALID_ARG;
+    return MBD_OK;
+}
+
+void wrap_positions(mbd_system *s, const double *pos) {
+    s->pos.resize(3 * (size_t)s->N);
+    for (int i = 0; i < s->N; ++i) {
+        double f[3];
+        for (int a = 0; a < 3; ++a) {
+            f[a] = s->recip[3 * a] * pos[3 * i] + s->recip[3 * a + 1] * pos[3 * i + 1] +
+                   s->recip[3 * a + 2] * pos[3 * i + 2];
+            f[a] -= std::floor(f[a]);
+            if (f[a] >= 1.0) f[a] -= 1.0;
+        }
+        for (int c = 0; c < 3; ++c)
+            s->pos[3 * i + c] = f[0] * s->cell[c] + f[1] * s->cell[3 + c] + f[2] * s->cell[6 + c];
+    }
+}
+
+// Full neighbour list over image pairs (i, j, n) with 0 < |R_i - R_j - n| < rmax
+// from a cell list: bins of perpendicular width >= rmax; bin offsets o map to
+// (o mod nbins, floor(o / nbins)) = (bin, image), so each (j, n) is visited once.
+mbd_status build_neighbors(mbd_system *s) {
+    const double rmax = std::max(s->r_cut, s->damp_cut);
+    const int N = s->N;
+    int nc[3], kk[3];
+    double width[3];
+    for (int a = 0; a < 3; ++a) {
+        const double rn = std::sqrt(s->recip[3 * a] * s->recip[3 * a] + s->recip[3 * a + 1] * s->recip[3 * a + 1] +
+                                    s->recip[3 * a + 2] * s->recip[3 * a + 2]);
+        width[a] = 1.0 / rn;
+        nc[a] = std::max(1, std::min(256, (int)std::floor(width[a] / rmax)));
+        kk[a] = (int)std::ceil(rmax * nc[a] / width[a] - 1e-12);
+        if (kk[a] > 120) return MBD_ERR_INVALID_ARG;
+    }
+    const int ncell = nc[0] * nc[1] * nc[2];
+    std::vector<int> bin(N), cstart(ncell + 1, 0), catoms(N);
+    std::vector<int> cidx(3 * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        int b[3];
+        for (int a = 0; a < 3; ++a) {
+            double f = s->recip[3 * a] * s->pos[3 * i] + s->recip[3 * a + 1] * s->pos[3 * i + 1] +
+                       s->recip[3 * a + 2] * s->pos[3 * i + 2];
+            f -= std::floor(f);
+            b[a] = std::min(nc[a] - 1, std::max(0, (int)std::floor(f * nc[a])));
+            cidx[3 * i + a] = b[a];
+        }
+        bin[i] = (b[0] * nc[1] + b[1]) * nc[2] + b[2];
+        cstart[bin[i] + 1]++;
+    }
+    for (int c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+    {
+        std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+        for (int i = 0; i < N; ++i) catoms[fill[bin[i]]++] = i;
+    }
+    const double r2max = rmax * rmax;
+    s->h_row.assign(N + 1, 0);
+    s->h_col.clear();
+    s->h_shift.clear();
+    for (int i = 0; i < N; ++i) {
+        const double *pi = &s->pos[3 * i];
+        for (int o0 = -kk[0]; o0 <= kk[0]; ++o0) {
+            const int t0 = cidx[3 * i] + o0;
+            const int n0 = (int)std::floor((double)t0 / nc[0]);
+            const int b0 = t0 - n0 * nc[0];
+            for (int o1 = -kk[1]; o1 <= kk[1]; ++o1) {
+                const int t1 = cidx[3 * i + 1] + o1;
+                const int n1 = (int)std::floor((double)t1 / nc[1]);
+                const int b1 = t1 - n1 * nc[1];
+                for (int o2 = -kk[2]; o2 <= kk[2]; ++o2) {
+                    const int t2 = cidx[3 * i + 2] + o2;
+                    const int n2 = (int)std::floor((double)t2 / nc[2]);
+                    const int b2 = t2 - n2 * nc[2];
+                    const int c = (b0 * nc[1] + b1) * nc[2] + b2;
+                    double sh[3];
+                    for (int x = 0; x < 3; ++x)
+                        sh[x] = n0 * s->cell[x] + n1 * s->cell[3 + x] + n2 * s->cell[6 + x];
+                    for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
+                        const int j = catoms[q];
+                        const double *pj = &s->pos[3 * j];
+                        const double rx = pi[0] - pj[0] - sh[0], ry = pi[1] - pj[1] - sh[1],
+                                     rz = pi[2] - pj[2] - sh[2];
+                        const double r2 = rx * rx + ry * ry + rz * rz;
+                        if (r2 < r2max && r2 > 0.0) {
+                            if (std::abs(n0) > 127 || std::abs(n1) > 127 || std::abs(n2) > 127)
+                                return MBD_ERR_INVALID_ARG;
+                            s->h_col.push_back(j);
+                            s->h_shift.push_back((n0 + 128) | ((n1 + 128) << 8) | ((n2 + 128) << 16));
+                        }
+                    }
+                }
+            }
+        }
+        s->h_row[i + 1] = (int)s->h_col.size();
+        if (s->h_col.size() > (size_t)0x7fffffff - 1024) return MBD_ERR_INVALID_ARG;
+    }
+    s->nnz = (long long)s->h_col.size();
+    MBD_TRY(s->row_d.ensure(sizeof(int) * (N + 1)));
+    MBD_TRY(s->col_d.ensure(sizeof(int) * std::max<size_t>(1, s->h_col.size())));
+    MBD_TRY(s->shift_d.ensure(sizeof(int) * std::max<size_t>(1, s->h_col.size())));
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->row_d.ptr, s->h_row.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice,
+                                 s->stream));
+    if (s->nnz > 0) {
+        MBD_CUDA_TRY(cudaMemcpyAsync(s->col_d.ptr, s->h_col.data(), sizeof(int) * s->h_col.size(),
+                                     cudaMemcpyHostToDevice, s->stream));
+        MBD_CUDA_TRY(cudaMemcpyAsync(s->shift_d.ptr, s->h_shift.data(), sizeof(int) * s->h_shift.size(),
+                                     cudaMemcpyHostToDevice, s->stream));
+    }
+    return MBD_OK;
+}
+
+// Bricks of the mesh for deterministic spreading; atoms are binned by the
+// brick of their last stencil point (top), read back from the device so that
+// the host and the kernels agree exactly.
+mbd_status build_bins(mbd_system *s) {
+    const int N = s->N;
+    std::vector<int> top(3 * (size_t)N);
+    MBD_CUDA_TRY(cudaMemcpyAsync(top.data(), s->top_d.ptr, sizeof(int) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    int bs[3], nb[3], ncand[3];
+    for (int a = 0; a < 3; ++a) {
+        const int K = s->K[a];
+        const int pref[5] = {4, 5, 3, 2, 1};
+        bs[a] = 1;
+        for (int e : pref)
+            if (K % e == 0) {
+                bs[a] = e;
+                break;
+            }
+        nb[a] = K / bs[a];
+        ncand[a] = std::min(nb[a], 1 + (bs[a] + s->p - 2) / bs[a]);
+    }
+    const int nbins = nb[0] * nb[1] * nb[2];
+    std::vector<int> start(nbins + 1, 0), atoms(N), bin(N);
+    for (int i = 0; i < N; ++i) {
+        const int t0 = top[3 * i] / bs[0], t1 = top[3 * i + 1] / bs[1], t2 = top[3 * i + 2] / bs[2];
+        bin[i] = (t0 * nb[1] + t1) * nb[2] + t2;
+        start[bin[i] + 1]++;
+    }
+    for (int b = 0; b < nbins; ++b) start[b + 1] += start[b];
+    {
+        std::vector<int> fill(start.begin(), start.end() - 1);
+        for (int i = 0; i < N; ++i) atoms[fill[bin[i]]++] = i;
+    }
+    MBD_TRY(s->bin_start_d.ensure(sizeof(int) * (nbins + 1)));
+    MBD_TRY(s->bin_atoms_d.ensure(sizeof(int) * N));
+    MBD_TRY(s->order_d.ensure(sizeof(int) * N));
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->bin_start_d.ptr, start.data(), sizeof(int) * (nbins + 1), cudaMemcpyHostToDevice,
+                                 s->stream));
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->bin_atoms_d.ptr, atoms.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s->stream));
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->order_d.ptr, atoms.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    BinView &B = s->bins;
+    B.nb1 = nb[0];
+    B.nb2 = nb[1];
+    B.nb3 = nb[2];
+    B.bs1 = bs[0];
+    B.bs2 = bs[1];
+    B.bs3 = bs[2];
+    B.nc1 = ncand[0];
+    B.nc2 = ncand[1];
+    B.nc3 = ncand[2];
+    B.start = s->bin_start_d.as<int>();
+    B.atoms = s->bin_atoms_d.as<int>();
+    return MBD_OK;
+}
+
+// M_p at the integers 0..p (recursion from M_2), for the B-spline moduli.
+void bspline_integers(int p, double *out) {
+    std::vector<double> cur(p + 1, 0.0), nxt(p + 1, 0.0);
+    cur[1] = 1.0;   // M_2(0) = 0, M_2(1) = 1, M_2(2) = 0
+    for (int n = 3; n <= p; ++n) {
+        for (int k = 0; k <= p; ++k) {
+            const double a = (k < p + 1) ? cur[k] : 0.0;
+            const double b = (k >= 1) ? cur[k - 1] : 0.0;
+            nxt[k] = (k * a + (n - k) * b) / (n - 1);
+        }
+        cur = nxt;
+    }
+    for (int k = 0; k <= p; ++k) out[k] = cur[k];
+}
+
+// |b(m)|^2 = 1 / |sum_{j=0}^{p-2} M_p(j+1) exp(2 pi i m j / K)|^2
+void bspline_moduli(int K, int p, double *out) {
+    std::vector<double> mi(p + 1);
+    bspline_integers(p, mi.data());
+    for (int m = 0; m < K; ++m) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j <= p - 2; ++j) {
+            const double ang = 2.0 * kPi * (double)((long long)m * j % K) / K;
+            re += mi[j + 1] * std::cos(ang);
+            im += mi[j + 1] * std::sin(ang);
+        }
+        out[m] = 1.0 / (re * re + im * im);
+    }
+}
+
+template <class T> mbd_status upload_twiddles(mbd_system *s) {
+    using C = typename Cplx<T>::type;
+    PrecData<T> &P = prec<T>(s);
+    DevBuf *tw[3] = {&P.tw1, &P.tw2, &P.tw3};
+    for (int a = 0; a < 3; ++a) {
+        const int K = s->K[a];
+        std::vector<C> h(K);
+        for (int n = 0; n < K; ++n) {
+            const double ang = 2.0 * kPi * n / K;
+            h[n].x = T(std::cos(ang));
+            h[n].y = T(-std::sin(ang));
+        }
+        MBD_TRY(tw[a]->ensure(sizeof(C) * K));
+        MBD_CUDA_TRY(cudaMemcpyAsync(tw[a]->ptr, h.data(), sizeof(C) * K, cudaMemcpyHostToDevice, s->stream));
+        MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    }
+    return MBD_OK;
+}
+
+template <class T> mbd_status setup_geometry(mbd_system *s) {
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->pos_d.ptr, s->pos.data(), sizeof(double) * 3 * s->N, cudaMemcpyHostToDevice,
+                                 s->stream));
+    MBD_TRY(build_neighbors(s));
+    MBD_TRY(launch_pair_tensors<T>(s, s->stream));
+    MBD_TRY(launch_splines<T>(s, s->stream));
+    MBD_TRY(build_bins(s));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return MBD_OK;
+}
+
+template <class T> mbd_status setup_mesh(mbd_system *s) {
+    std::vector<double> bm(s->K[0] + s->K[1] + s->K[2]);
+    bspline_moduli(s->K[0], s->p, bm.data());
+    bspline_moduli(s->K[1], s->p, bm.data() + s->K[0]);
+    bspline_moduli(s->K[2], s->p, bm.data() + s->K[0] + s->K[1]);
+    MBD_TRY(launch_influence<T>(s, bm.data(), s->stream));
+    MBD_TRY(upload_twiddles<T>(s));
+    return MBD_OK;
+}
+
+mbd_status create_impl(const mbd_system_desc *d, void *stream, mbd_system **out) {
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) {
+        if (e != cudaSuccess) set_last_error("cudaGetDeviceCount", e);
+        cudaGetLastError();
+        return MBD_ERR_NO_DEVICE;
+    }
+    mbd_system *s = new (std::nothrow) mbd_system();
+    if (!s) return MBD_ERR_OOM;
+    s->N = d->n_atoms;
+    std::memcpy(s->cell, d->cell, sizeof(s->cell));
+    // reciprocal rows a*_alpha with a*_alpha . a_beta = delta: inverse transpose of the cell
+    const double *c = s->cell;
+    const double det = c[0] * (c[4] * c[8] - c[5] * c[7]) - c[1] * (c[3] * c[8] - c[5] * c[6]) +
+                       c[2] * (c[3] * c[7] - c[4] * c[6]);
+    s->volume = det;
+    double inv[9];
+    inv[0] = (c[4] * c[8] - c[5] * c[7]) / det;
+    inv[1] = (c[2] * c[7] - c[1] * c[8]) / det;
+    inv[2] = (c[1] * c[5] - c[2] * c[4]) / det;
+    inv[3] = (c[5] * c[6] - c[3] * c[8]) / det;
+    inv[4] = (c[0] * c[8] - c[2] * c[6]) / det;
+    inv[5] = (c[2] * c[3] - c[0] * c[5]) / det;
+    inv[6] = (c[3] * c[7] - c[4] * c[6]) / det;
+    inv[7] = (c[1] * c[6] - c[0] * c[7]) / det;
+    inv[8] = (c[0] * c[4] - c[1] * c[3]) / det;
+    // recip row alpha = column alpha of inv (cell^-1)
+    for (int a = 0; a < 3; ++a)
+        for (int x = 0; x < 3; ++x) s->recip[3 * a + x] = inv[3 * x + a];
+    for (int a = 0; a < 3; ++a) {
+        s->K[a] = d->mesh[a];
+        factor_mesh(s->K[a], s->fft[a]);
+    }
+    s->p = d->spline_order;
+    s->ewald_beta = d->ewald_beta;
+    s->r_cut = d->r_cut;
+    s->damp_cut = d->damp_cut > 0.0 ? d->damp_cut : d->r_cut;
+    s->damp_beta = d->damp_beta;
+    s->damp_d = d->damp_d;
+    s->precision = d->precision;
+    s->stream = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)s->N;
+    s->alpha.assign(d->alpha, d->alpha + n);
+    s->omega.assign(d->omega, d->omega + n);
+    s->rvdw.assign(d->r_vdw, d->r_vdw + n);
+    s->omega_sum = 0.0;
+    for (size_t i = 0; i < n; ++i) s->omega_sum += s->omega[i];
+    wrap_positions(s, d->pos);
+    std::vector<double> g(n), w2(n);
+    for (size_t i = 0; i < n; ++i) {
+        g[i] = s->omega[i] * std::sqrt(s->alpha[i]);
+        w2[i] = s->omega[i] * s->omega[i];
+    }
+    auto fail = [&](mbd_status st) {
+        mbd_destroy_system(s);
+        return st;
+    };
+    mbd_status st;
+    if ((st = s->pos_d.ensure(sizeof(double) * 3 * n)) != MBD_OK) return fail(st);
+    if ((st = s->g_d.ensure(sizeof(double) * n)) != MBD_OK) return fail(st);
+    if ((st = s->w2_d.ensure(sizeof(double) * n)) != MBD_OK) return fail(st);
+    if ((st = s->rvdw_d.ensure(sizeof(double) * n)) != MBD_OK) return fail(st);
+    if ((st = s->top_d.ensure(sizeof(int) * 3 * n)) != MBD_OK) return fail(st);
+    if (cudaMallocHost(&s->host_scal, 16 * sizeof(double)) != cudaSuccess) {
+        s->host_scal = nullptr;
+        cudaGetLastError();
+        return fail(MBD_ERR_OOM);
+    }
+    if (cudaMallocHost(&s->host_status, 4 * sizeof(int)) != cudaSuccess) {
+        s->host_status = nullptr;
+        cudaGetLastError();
+        return fail(MBD_ERR_OOM);
+    }
+    cudaError_t ce;
+    if ((ce = cudaMemcpyAsync(s->g_d.ptr, g.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) ||
+        (ce = cudaMemcpyAsync(s->w2_d.ptr, w2.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) ||
+        (ce = cudaMemcpyAsync(s->rvdw_d.ptr, s->rvdw.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
+                              s->stream)) ||
+        (ce = cudaStreamSynchronize(s->stream))) {
+        set_last_error("upload", ce);
+        return fail(MBD_ERR_CUDA);
+    }
+    if (s->precision == MBD_FP64) {
+        if ((st = setup_geometry<double>(s)) != MBD_OK) return fail(st);
+        if ((st = setup_mesh<double>(s)) != MBD_OK) return fail(st);
+    } else {
+        if ((st = setup_geometry<float>(s)) != MBD_OK) return fail(st);
+        if ((st = setup_mesh<float>(s)) != MBD_OK) return fail(st);
+    }
+    *out = s;
+    return MBD_OK;
+}
+
+// ---------------------------------------------------------------- Lanczos workspace
+struct Lz {
+    LanczosView v;
+    int R, ld, m, rows, nblk;
+};
+
+mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nblk, Lz &z) {
+    z.R = R;
+    z.ld = probe_ld(R);
+    z.m = m;
+    z.rows = rows;
+    z.nblk = std::max(1, std::min((rows + 63) / 64, 2048));
+    const size_t ld = z.ld;
+    const int nchunk = (z.ld + 31) / 32;
+    MBD_TRY(s->Y.ensure(sizeof(double) * (size_t)m * rows * ld));
+    MBD_TRY(s->L.ensure(sizeof(double) * (size_t)rows * ld));
+    MBD_TRY(s->a.ensure(sizeof(double) * (size_t)m * ld));
+    MBD_TRY(s->b.ensure(sizeof(double) * (size_t)m * ld));
+    MBD_TRY(s->invb.ensure(sizeof(double) * ld));
+    MBD_TRY(s->length.ensure(sizeof(int) * ld));
+    MBD_TRY(s->partial.ensure(sizeof(double) * (size_t)std::max(z.nblk, field_nblk) * ld));
+    const size_t cbytes = sizeof(unsigned) * (size_t)std::max(nchunk, 64);
+    if (s->counter.bytes < cbytes) {
+        MBD_TRY(s->counter.ensure(cbytes));
+        MBD_CUDA_TRY(cudaMemsetAsync(s->counter.ptr, 0, s->counter.bytes, s->stream));
+    }
+    MBD_TRY(s->q.ensure(sizeof(double) * ld));
+    MBD_TRY(s->scal.ensure(sizeof(double) * 16));
+    MBD_TRY(s->status.ensure(sizeof(int) * 4));
+    MBD_TRY(s->work.ensure(sizeof(double) * (size_t)(2 * m + m * m) * R));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->a.ptr, 0, sizeof(double) * (size_t)m * ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->b.ptr, 0, sizeof(double) * (size_t)m * ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
+    z.v.Y = s->Y.as<double>();
+    z.v.L = s->L.as<double>();
+    z.v.a = s->a.as<double>();
+    z.v.b = s->b.as<double>();
+    z.v.invb = s->invb.as<double>();
+    z.v.length = s->length.as<int>();
+    z.v.partial = s->partial.as<double>();
+    z.v.counter = s->counter.as<unsigned>();
+    return MBD_OK;
+}
+
+template <class T> mbd_status ensure_mesh(mbd_system *s, int ld) {
+    PrecData<T> &P = prec<T>(s);
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    MBD_TRY(P.d.ensure(sizeof(T) * 3 * (size_t)s->N * ld));
+    MBD_TRY(P.mesh.ensure(sizeof(T) * npts * ld));
+    return MBD_OK;
+}
+
+// Algorithm 1 with Algorithm 2 per step: m Lanczos steps for all R probes.
+template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t seed, Lz &z) {
+    const int rows = 3 * s->N;
+    MBD_TRY(lanczos_workspace(s, R, m, rows, field_blocks(s->N), z));
+    MBD_TRY(ensure_mesh<T>(s, z.ld));
+    PrecData<T> &P = prec<T>(s);
+    FieldOut<T> fo;
+    fo.mode = kFieldLanczos;
+    fo.terms = MBD_TERM_ALL;
+    fo.out = nullptr;
+    fo.xin = nullptr;
+    fo.lz = z.v;
+    for (int k = 0; k < m; ++k) {
+        MBD_TRY(launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
+                                  (int)sizeof(T), z.nblk));
+        MBD_TRY(launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
+        MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), z.ld));
+        fo.k = k;
+        MBD_TRY(launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
+    }
+    MBD_TRY(launch_quadrature_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), s->status.as<int>(),
+                                s->work.as<double>(), s->stream));
+    MBD_TRY(launch_energy_reduce(s->q.as<double>(), R, rows, s->omega_sum, s->scal.as<double>(), s->stream));
+    return MBD_OK;
+}
+
+mbd_status status_from_bits(int bits) {
+    if (bits & 1) return MBD_ERR_NOT_POSITIVE_DEFINITE;
+    if (bits & 6) return MBD_ERR_NONFINITE;
+    return MBD_OK;
+}
+
+// Copy energy, trace, status, and optionally q and (a, b) to the host.
+mbd_status fetch_results(mbd_system *s, const Lz &z, double *energy, double *trace, double *q_host,
+                         double *ab_host) {
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->host_scal, s->scal.ptr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->host_status, s->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<double> qv, av, bv;
+    if (q_host) {
+        qv.resize(z.R);
+        MBD_CUDA_TRY(cudaMemcpyAsync(qv.data(), s->q.ptr, sizeof(double) * z.R, cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (ab_host) {
+        av.resize((size_t)z.m * z.ld);
+        bv.resize((size_t)z.m * z.ld);
+        MBD_CUDA_TRY(cudaMemcpyAsync(av.data(), s->a.ptr, sizeof(double) * av.size(), cudaMemcpyDeviceToHost,
+                                     s->stream));
+        MBD_CUDA_TRY(cudaMemcpyAsync(bv.data(), s->b.ptr, sizeof(double) * bv.size(), cudaMemcpyDeviceToHost,
+                                     s->stream));
+    }
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    const mbd_status st = status_from_bits(*s->host_status);
+    if (st != MBD_OK) return st;
+    if (!std::isfinite(s->host_scal[0])) return MBD_ERR_NONFINITE;
+    *energy = s->host_scal[0];
+    if (trace) *trace = s->host_scal[1];
+    if (q_host) std::memcpy(q_host, qv.data(), sizeof(double) * z.R);
+    if (ab_host) {
+        for (int r = 0; r < z.R; ++r)
+            for (int k = 0; k < z.m; ++k) {
+                ab_host[((size_t)r * 2) * z.m + k] = av[(size_t)k * z.ld + r];
+                ab_host[((size_t)r * 2 + 1) * z.m + k] = bv[(size_t)k * z.ld + r];
+            }
+    }
+    return MBD_OK;
+}
+
+template <class T>
+mbd_status energy_impl(mbd_system *s, int R, int m, uint64_t seed, double *energy, double *trace, double *q_host,
+                       double *ab_host) {
+    Lz z;
+    MBD_TRY(run_lanczos<T>(s, R, m, seed, z));
+    return fetch_results(s, z, energy, trace, q_host, ab_host);
+}
+
+template <class T>
+mbd_status forces_impl(mbd_system *s, int R, int m, uint64_t seed, double *energy, double *forces_dev) {
+    Lz z;
+    MBD_TRY(run_lanczos<T>(s, R, m, seed, z));
+    // w_l = C^{-1/2} v_l = sum_k c_lk y_lk; coefficients from the full eigenvectors of Delta_l
+    MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
+    MBD_TRY(launch_inv_sqrt_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->work2.as<double>(), s->status.as<int>(),
+                              s->work.as<double>(), s->stream));
+    PrecData<T> &P = prec<T>(s);
+    const int ld2 = 2 * R;
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    MBD_TRY(P.d.ensure(sizeof(T) * 3 * (size_t)s->N * std::max(ld2, z.ld)));
+    MBD_TRY(P.mesh.ensure(sizeof(T) * npts * std::max(ld2, z.ld)));
+    MBD_TRY(launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m, P.d.template as<T>(),
+                                      ld2));
+    MBD_TRY(launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));
+    MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), ld2));
+    const double scale = 0.25 * (3.0 * s->N) / R;
+    MBD_TRY(launch_force_gather_t<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, ld2, scale, forces_dev));
+    return fetch_results(s, z, energy, nullptr, nullptr, nullptr);
+}
+
+template <class T> mbd_status apply_impl(mbd_system *s, int nvec, const double *x, double *y, int terms, bool field) {
+    const int rows = 3 * s->N;
+    const int ld = probe_ld(nvec);
+    MBD_TRY(ensure_mesh<T>(s, ld));
+    MBD_TRY(s->L.ensure(sizeof(double) * (size_t)rows * ld));
+    MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)rows * ld));
+    double *xt = s->L.as<double>();
+    double *yt = s->work2.as<double>();
+    PrecData<T> &P = prec<T>(s);
+    MBD_CUDA_TRY(cudaMemsetAsync(xt, 0, sizeof(double) * (size_t)rows * ld, s->stream));
+    MBD_TRY(launch_to_probe_major(x, nvec, rows, xt, ld, s->stream));
+    if (field) {
+        MBD_TRY(launch_cast_rows<T>(xt, P.d.template as<T>(), (size_t)rows * ld, s->stream));
+    } else {
+        MBD_TRY(launch_gscale<T>(xt, s->g_d.as<double>(), P.d.template as<T>(), rows, ld, s->stream));
+    }
+    if (terms & MBD_TERM_RECIP) {
+        MBD_TRY(launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld));
+        MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), ld));
+    }
+    FieldOut<T> fo;
+    fo.mode = field ? kFieldOut : kFieldApply;
+    fo.terms = terms;
+    fo.out = yt;
+    fo.xin = xt;
+    fo.k = 0;
+    std::memset(&fo.lz, 0, sizeof(fo.lz));
+    MBD_TRY(launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld, fo));
+    MBD_TRY(launch_from_probe_major(yt, nvec, rows, ld, y, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return MBD_OK;
+}
+
+template <class T> mbd_status spread_impl(mbd_system *s, int nvec, const double *d, double *mesh_out) {
+    const int rows = 3 * s->N;
+    const int ld = probe_ld(nvec);
+    MBD_TRY(ensure_mesh<T>(s, ld));
+    MBD_TRY(s->L.ensure(sizeof(double) * (size_t)rows * ld));
+    double *xt = s->L.as<double>();
+    PrecData<T> &P = prec<T>(s);
+    MBD_CUDA_TRY(cudaMemsetAsync(xt, 0, sizeof(double) * (size_t)rows * ld, s->stream));
+    MBD_TRY(launch_to_probe_major(d, nvec, rows, xt, ld, s->stream));
+    MBD_TRY(launch_cast_rows<T>(xt, P.d.template as<T>(), (size_t)rows * ld, s->stream));
+    MBD_TRY(launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld));
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    MBD_TRY(launch_mesh_out<T>(P.mesh.template as<T>(), nvec, npts, ld, mesh_out, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return MBD_OK;
+}
+
+template <class T> mbd_status convolve_impl(mbd_system *s, int nvec, const double *in, double *out) {
+    const int ld = probe_ld(nvec);
+    MBD_TRY(ensure_mesh<T>(s, ld));
+    PrecData<T> &P = prec<T>(s);
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    MBD_TRY(launch_mesh_in<T>(in, nvec, npts, ld, P.mesh.template as<T>(), s->stream));
+    MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), ld));
+    MBD_TRY(launch_mesh_out<T>(P.mesh.template as<T>(), nvec, npts, ld, out, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return MBD_OK;
+}
+
+mbd_status check_run_args(mbd_system *s, int R, int m, double *energy) {
+    if (!s || !energy) return MBD_ERR_INVALID_ARG;
+    if (R < 1 || R > (1 << 20) || m < 1 || m > kMaxSteps) return MBD_ERR_INVALID_ARG;
+    return MBD_OK;
+}
+
+}  // namespace
+}  // namespace mbd
+
+using namespace mbd;
+
+extern "C" {
+
+const char *mbd_status_string(mbd_status st) {
+    switch (st) {
+        case MBD_OK: return "MBD_OK";
+        case MBD_ERR_INVALID_ARG: return "MBD_ERR_INVALID_ARG";
+        case MBD_ERR_OOM: return "MBD_ERR_OOM";
+        case MBD_ERR_CUDA: return "MBD_ERR_CUDA";
+        case MBD_ERR_NOT_POSITIVE_DEFINITE: return "MBD_ERR_NOT_POSITIVE_DEFINITE";
+        case MBD_ERR_NONFINITE: return "MBD_ERR_NONFINITE";
+        case MBD_ERR_TIMEOUT: return "MBD_ERR_TIMEOUT";
+        case MBD_ERR_UNSUPPORTED: return "MBD_ERR_UNSUPPORTED";
+        case MBD_ERR_NO_DEVICE: return "MBD_ERR_NO_DEVICE";
+    }
+    return "MBD_ERR_UNKNOWN";
+}
+
+const char *mbd_last_error(void) { return g_last_error.c_str(); }
+
+mbd_status mbd_create_system(const mbd_system_desc *desc, void *cuda_stream, mbd_system **out) {
+    if (out == nullptr) return MBD_ERR_INVALID_ARG;
+    MBD_TRY(validate(desc));
+    return create_impl(desc, cuda_stream, out);
+}
+
+void mbd_destroy_system(mbd_system *sys) {
+    if (sys == nullptr) return;
+    if (sys->host_scal) cudaFreeHost(sys->host_scal);
+    if (sys->host_status) cudaFreeHost(sys->host_status);
+    delete sys;
+}
+
+mbd_status mbd_update_positions(mbd_system *s, const double *pos) {
+    if (!s || !pos || !finite_all(pos, 3 * (size_t)s->N)) return MBD_ERR_INVALID_ARG;
+    wrap_positions(s, pos);
+    if (s->precision == MBD_FP64) return setup_geometry<double>(s);
+    return setup_geometry<float>(s);
+}
+
+mbd_status mbd_apply_C(mbd_system *s, int32_t nvec, const double *x_dev, double *y_dev) {
+    if (!s || !x_dev || !y_dev || nvec < 1 || nvec > (1 << 20) || x_dev == y_dev) return MBD_ERR_INVALID_ARG;
+    if (s->precision == MBD_FP64) return apply_impl<double>(s, nvec, x_dev, y_dev, MBD_TERM_ALL, false);
+    return apply_impl<float>(s, nvec, x_dev, y_dev, MBD_TERM_ALL, false);
+}
+
+mbd_status mbd_field(mbd_system *s, int32_t nvec, const double *d_dev, double *e_dev, int32_t terms) {
+    if (!s || !d_dev || !e_dev || nvec < 1 || nvec > (1 << 20) || d_dev == e_dev) return MBD_ERR_INVALID_ARG;
+    if (terms < 0 || terms > MBD_TERM_ALL) return MBD_ERR_INVALID_ARG;
+    if (s->precision == MBD_FP64) return apply_impl<double>(s, nvec, d_dev, e_dev, terms, true);
+    return apply_impl<float>(s, nvec, d_dev, e_dev, terms, true);
+}
+
+mbd_status mbd_spread(mbd_system *s, int32_t nvec, const double *d_dev, double *mesh_dev) {
+    if (!s || !d_dev || !mesh_dev || nvec < 1 || nvec > (1 << 16)) return MBD_ERR_INVALID_ARG;
+    if (s->precision == MBD_FP64) return spread_impl<double>(s, nvec, d_dev, mesh_dev);
+    return spread_impl<float>(s, nvec, d_dev, mesh_dev);
+}
+
+mbd_status mbd_convolve(mbd_system *s, int32_t nvec, const double *in_dev, double *out_dev) {
+    if (!s || !in_dev || !out_dev || nvec < 1 || nvec > (1 << 16)) return MBD_ERR_INVALID_ARG;
+    if (s->precision == MBD_FP64) return convolve_impl<double>(s, nvec, in_dev, out_dev);
+    return convolve_impl<float>(s, nvec, in_dev, out_dev);
+}
+
+mbd_status mbd_lanczos_energy(mbd_system *s, int32_t R, int32_t m, uint64_t seed, double *energy, double *trace,
+                              double *q_host, double *ab_host) {
+    MBD_TRY(check_run_args(s, R, m, energy));
+    if (s->precision == MBD_FP64) return energy_impl<double>(s, R, m, seed, energy, trace, q_host, ab_host);
+    return energy_impl<float>(s, R, m, seed, energy, trace, q_host, ab_host);
+}
+
+mbd_status mbd_energy_forces(mbd_system *s, int32_t R, int32_t m, uint64_t seed, double *energy,
+                             double *forces_dev) {
+    MBD_TRY(check_run_args(s, R, m, energy));
+    if (!forces_dev) return MBD_ERR_INVALID_ARG;
+    if (s->precision == MBD_FP64) return forces_impl<double>(s, R, m, seed, energy, forces_dev);
+    return forces_impl<float>(s, R, m, seed, energy, forces_dev);
+}
+
+mbd_status mbd_generate_probes(uint64_t seed, int32_t first, int32_t R, int32_t dim, double *v_dev) {
+    if (!v_dev || R < 1 || dim < 1 || first < 0) return MBD_ERR_INVALID_ARG;
+    MBD_TRY(launch_probes(seed, first, R, dim, v_dev, nullptr));
+    MBD_CUDA_TRY(cudaStreamSynchronize(nullptr));
+    return MBD_OK;
+}
+
+mbd_status mbd_tridiag_quadrature(int32_t R, int32_t m, const double *a_host, const double *b_host,
+                                  double *q_host) {
+    if (!a_host || !b_host || !q_host || R < 1 || m < 1 || m > kMaxSteps) return MBD_ERR_INVALID_ARG;
+    std::vector<double> a((size_t)m * R), b((size_t)m * R);
+    std::vector<int> len(R);
+    for (int r = 0; r < R; ++r) {
+        int n = m;
+        for (int k = 0; k < m - 1; ++k)
+            if (b_host[(size_t)r * m + k] == 0.0) {
+                n = k + 1;
+                break;
+            }
+        len[r] = n;
+        for (int k = 0; k < m; ++k) {
+            a[(size_t)k * R + r] = a_host[(size_t)r * m + k];
+            b[(size_t)k * R + r] = b_host[(size_t)r * m + k];
+        }
+    }
+    DevBuf da, db, dl, dq, dst, dw;
+    MBD_TRY(da.ensure(sizeof(double) * a.size()));
+    MBD_TRY(db.ensure(sizeof(double) * b.size()));
+    MBD_TRY(dl.ensure(sizeof(int) * R));
+    MBD_TRY(dq.ensure(sizeof(double) * R));
+    MBD_TRY(dst.ensure(sizeof(int)));
+    MBD_TRY(dw.ensure(sizeof(double) * 3 * (size_t)m * R));
+    MBD_CUDA_TRY(cudaMemcpy(da.ptr, a.data(), sizeof(double) * a.size(), cudaMemcpyHostToDevice));
+    MBD_CUDA_TRY(cudaMemcpy(db.ptr, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice));
+    MBD_CUDA_TRY(cudaMemcpy(dl.ptr, len.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
+    MBD_CUDA_TRY(cudaMemset(dst.ptr, 0, sizeof(int)));
+    MBD_TRY(launch_quadrature_t(da.as<double>(), db.as<double>(), dl.as<int>(), R, R, m, dq.as<double>(),
+                                dst.as<int>(), dw.as<double>(), nullptr));
+    int bits = 0;
+    MBD_CUDA_TRY(cudaMemcpy(&bits, dst.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    MBD_TRY(status_from_bits(bits));
+    MBD_CUDA_TRY(cudaMemcpy(q_host, dq.ptr, sizeof(double) * R, cudaMemcpyDeviceToHost));
+    return MBD_OK;
+}
+
+mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double omega_sum, int32_t R, int32_t m,
+                                    uint64_t seed, double *energy, double *q_host, double *ab_host) {
+    if (!c_dev || !energy || dim < 1 || R < 1 || m < 1 || m > kMaxSteps) return MBD_ERR_INVALID_ARG;
+    // a throwaway system object holds the workspace; no geometry
+    mbd_system *s = new (std::nothrow) mbd_system();
+    if (!s) return MBD_ERR_OOM;
+    s->N = (dim + 2) / 3;
+    s->stream = nullptr;
+    s->omega_sum = omega_sum;
+    auto run = [&]() -> mbd_status {
+        if (cudaMallocHost(&s->host_scal, 16 * sizeof(double)) != cudaSuccess) return MBD_ERR_OOM;
+        if (cudaMallocHost(&s->host_status, 4 * sizeof(int)) != cudaSuccess) return MBD_ERR_OOM;
+        Lz z;
+        MBD_TRY(lanczos_workspace(s, R, m, dim, 1, z));
+        MBD_TRY(s->f64.d.ensure(sizeof(double) * (size_t)dim * z.ld));
+        MBD_TRY(s->g_d.ensure(sizeof(double) * ((size_t)dim / 3 + 1)));
+        // g = 1 so that the prologue's d output is y* itself (unused by the dense operator)
+        std::vector<double> ones((size_t)dim / 3 + 1, 1.0);
+        MBD_CUDA_TRY(cudaMemcpy(s->g_d.ptr, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice));
+        for (int k = 0; k < m; ++k) {
+            MBD_TRY(launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, dim, s->g_d.as<double>(), s->f64.d.ptr, 8,
+                                      z.nblk));
+            MBD_TRY(launch_dense_step(c_dev, dim, z.v, k, R, z.ld, z.nblk, s->stream));
+        }
+        MBD_TRY(launch_quadrature_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), s->status.as<int>(),
+                                    s->work.as<double>(), s->stream));
+        MBD_TRY(launch_energy_reduce(s->q.as<double>(), R, dim, omega_sum, s->scal.as<double>(), s->stream));
+        return fetch_results(s, z, energy, nullptr, q_host, ab_host);
+    };
+    const mbd_status st = run();
+    mbd_destroy_system(s);
+    return st;
+}
+
+mbd_status mbd_get_info(const mbd_system *s, mbd_info *info) {
+    if (!s || !info) return MBD_ERR_INVALID_ARG;
+    info->n_atoms = s->N;
+    for (int a = 0; a < 3; ++a) info->mesh[a] = s->K[a];
+    info->n_pairs = s->nnz;
+    info->precision = s->precision;
+    long long bytes = 0;
+    const DevBuf *bufs[] = {&s->pos_d, &s->g_d, &s->w2_d, &s->rvdw_d, &s->row_d, &s->col_d, &s->shift_d,
+                            &s->top_d, &s->bin_start_d, &s->bin_atoms_d, &s->order_d, &s->Y, &s->L, &s->a, &s->b,
+                            &s->invb, &s->length, &s->partial, &s->counter, &s->q, &s->scal, &s->status, &s->work,
+                            &s->work2, &s->f64.pairA, &s->f64.w, &s->f64.dw, &s->f64.d2w, &s->f64.G, &s->f64.d,
+                            &s->f64.mesh, &s->f32.pairA, &s->f32.w, &s->f32.dw, &s->f32.d2w, &s->f32.G, &s->f32.d,
+                            &s->f32.mesh};
+    for (const DevBuf *b : bufs) bytes += (long long)b->bytes;
+    info->device_bytes = bytes;
+    return MBD_OK;
+}
+
+}  // extern "C"

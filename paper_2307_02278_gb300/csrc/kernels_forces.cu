@@ -1,0 +1,274 @@
+// Force kernels.  The paper computes energies only (its Conclusions name the
+// gradients as the next step); with alpha and omega position-independent,
+//   dE/dR = (1/4) Tr(C^{-1/2} dC/dR) ~ (1/4)(D/R) sum_l grad_R [p_l^T T'(R) q_l],
+// p_l = g . w_l, q_l = g . v_l, w_l = C^{-1/2} v_l = sum_k c_{lk} y_{lk}.
+// The probes' p and q are interleaved as one complex probe pair, so the SPME
+// part reuses the spread and FFT convolution kernels with 2R "probes":
+//   phi_p + i phi_q = F^-1[G F[D_p + i D_q]],
+// and grad_i = sum_k H_i(k) [p_i phi_q(k) + q_i phi_p(k)] with H_i the Hessian
+// of the stencil weight W_i(k) wrt R_i; the real-space part contracts the
+// derivative of the pair tensor, dA_ab/dr_c, with p_i q_j + p_j q_i.
+#include "mbd_internal.cuh"
+
+namespace mbd {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr double kSqrtPi = 1.77245385090551602730;
+
+template <class T>
+__global__ void k_force_dipoles(int rows, const double *__restrict__ Y, const double *__restrict__ coef,
+                                const int *__restrict__ length, const double *__restrict__ g, int R, int ld, int m,
+                                T *__restrict__ dpq, int ld2) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * R) return;
+    const int row = (int)(idx / R), r = (int)(idx % R);
+    const size_t stride = (size_t)rows * ld;
+    const int n = length[r];
+    double w = 0.0;
+    for (int k = 0; k < n; ++k) w += coef[(size_t)k * ld + r] * Y[(size_t)k * stride + (size_t)row * ld + r];
+    const double gi = g[row / 3];
+    dpq[(size_t)row * ld2 + 2 * r] = T(gi * w);
+    dpq[(size_t)row * ld2 + 2 * r + 1] = T(gi * Y[(size_t)row * ld + r]);
+}
+
+template <class T> struct ForceArgs {
+    const T *dpq;        // [N][3][ld2] (p_l, q_l) interleaved
+    const T *mesh;       // [K^3][ld2] (phi_p, phi_q) interleaved
+    int R, ld2;
+    Geom g;
+    const int *top;
+    const T *w, *dw, *d2w;
+    const int *row, *col, *shift;
+    const double *pos, *rvdw;
+    double beta, r_cut, damp_cut, damp_beta, damp_d;
+    double scale;
+    double *forces;      // [N][3] FP64
+};
+
+// dA_ab / dr_c for the real-space pair tensor (FP64):
+//   erfc part  -B2 (delta_ab r_c + delta_ac r_b + delta_bc r_a) + B3 r_a r_b r_c
+//   damping    -d/dr_c [(1 - s) T_ab] with T_ab = delta_ab/r^3 - 3 r_a r_b / r^5
+__device__ void pair_tensor_grad_impl(double rx, double ry, double rz, double rsum, double beta, double r_cut,
+                                      double damp_cut, double damp_beta, double damp_d, double out[18]) {
+    const double rv[3] = {rx, ry, rz};
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const double rho = sqrt(r2);
+    // A = c_id I - c_rr r r^T with radial c_id, c_rr; dA_ab/dr_c =
+    //   (c_id'/rho) r_c delta_ab - (c_rr'/rho) r_c r_a r_b - c_rr (delta_ac r_b + delta_bc r_a)
+    double cid_p = 0.0, crr = 0.0, crr_p = 0.0;   // c_id'/rho, c_rr, c_rr'/rho
+    if (rho < r_cut) {
+        const double e = exp(-beta * beta * r2);
+        const double b0 = erfc(beta * rho) / rho;
+        const double b1 = (b0 + 2.0 * beta / kSqrtPi * e) / r2;
+        const double b2 = (3.0 * b1 + 4.0 * beta * beta * beta / kSqrtPi * e) / r2;
+        const double b3 = (5.0 * b2 + 8.0 * beta * beta * beta * beta * beta / kSqrtPi * e) / r2;
+        // (1/r) dB_n/dr = -B_{n+1}
+        cid_p += -b2;
+        crr += b2;
+        crr_p += -b3;
+    }
+    if (rho < damp_cut) {
+        const double x = damp_d * (rho / (damp_beta * rsum) - 1.0);
+        const double oms = 1.0 / (1.0 + exp(x));          // 1 - s
+        const double s = 1.0 - oms;
+        const double dsdr = damp_d / (damp_beta * rsum) * s * oms;
+        const double r3 = r2 * rho, r5 = r3 * r2;
+        // subtract (1-s) T:  c_id -= oms / r^3,  c_rr -= 3 oms / r^5
+        // d/dr (oms / r^3) = -dsdr / r^3 - 3 oms / r^4 ;  d/dr (3 oms / r^5) = -3 dsdr / r^5 - 15 oms / r^6
+        cid_p -= (-dsdr / r3 - 3.0 * oms / (r3 * rho)) / rho;
+        crr -= 3.0 * oms / r5;
+        crr_p -= (-3.0 * dsdr / r5 - 15.0 * oms / (r5 * rho)) / rho;
+    }
+    int o = 0;
+    for (int ab = 0; ab < 6; ++ab) {
+        const int ia = ab < 3 ? 0 : (ab < 5 ? 1 : 2);
+        const int ib = ab < 3 ? ab : (ab < 5 ? ab - 2 : 2);
+        for (int c = 0; c < 3; ++c) {
+            double v = -crr_p * rv[c] * rv[ia] * rv[ib];
+            if (ia == ib) v += cid_p * rv[c];
+            if (ia == c) v -= crr * rv[ib];
+            if (ib == c) v -= crr * rv[ia];
+            out[o++] = v;
+        }
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWarps * 32) k_force_gather(ForceArgs<T> a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kWarps + warp;
+    if (i >= a.g.N) return;
+    const int p = a.g.p;
+    const double *cm = a.g.cmat;
+    // ---- SPME: acc_beta = sum_k sum_l H_u(k)_{beta gamma} (e_p,gamma phi_q + e_q,gamma phi_p)
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    {
+        const int top1 = a.top[3 * i], top2 = a.top[3 * i + 1], top3 = a.top[3 * i + 2];
+        const T *w = a.w + (size_t)3 * p * i, *dw = a.dw + (size_t)3 * p * i, *d2w = a.d2w + (size_t)3 * p * i;
+        for (int l = lane; l < a.R; l += 32) {
+            // scaled-fractional components e = C x of p_i and q_i
+            T pc[3], qc[3];
+            for (int c = 0; c < 3; ++c) {
+                pc[c] = a.dpq[(size_t)(3 * i + c) * a.ld2 + 2 * l];
+                qc[c] = a.dpq[(size_t)(3 * i + c) * a.ld2 + 2 * l + 1];
+            }
+            T ep[3], eq[3];
+            for (int b = 0; b < 3; ++b) {
+                ep[b] = T(cm[3 * b]) * pc[0] + T(cm[3 * b + 1]) * pc[1] + T(cm[3 * b + 2]) * pc[2];
+                eq[b] = T(cm[3 * b]) * qc[0] + T(cm[3 * b + 1]) * qc[1] + T(cm[3 * b + 2]) * qc[2];
+            }
+            T h0 = T(0), h1 = T(0), h2 = T(0);
+            for (int t1 = 0; t1 < p; ++t1) {
+                int k1 = top1 - t1;
+                if (k1 < 0) k1 += a.g.K1;
+                const T wa = w[t1], da = dw[t1], ea = d2w[t1];
+                for (int t2 = 0; t2 < p; ++t2) {
+                    int k2 = top2 - t2;
+                    if (k2 < 0) k2 += a.g.K2;
+                    const T wb = w[p + t2], db = dw[p + t2], eb = d2w[p + t2];
+                    const size_t rowbase = ((size_t)k1 * a.g.K2 + k2) * a.g.K3;
+                    for (int t3 = 0; t3 < p; ++t3) {
+                        int k3 = top3 - t3;
+                        if (k3 < 0) k3 += a.g.K3;
+                        const T wc = w[2 * p + t3], dc = dw[2 * p + t3], ec = d2w[2 * p + t3];
+                        const size_t o = (rowbase + k3) * a.ld2 + 2 * l;
+                        const T fp = a.mesh[o], fq = a.mesh[o + 1];
+                        const T u0 = ep[0] * fq + eq[0] * fp;
+                        const T u1 = ep[1] * fq + eq[1] * fp;
+                        const T u2 = ep[2] * fq + eq[2] * fp;
+                        const T H00 = ea * wb * wc, H11 = wa * eb * wc, H22 = wa * wb * ec;
+                        const T H01 = da * db * wc, H02 = da * wb * dc, H12 = wa * db * dc;
+                        h0 += H00 * u0 + H01 * u1 + H02 * u2;
+                        h1 += H01 * u0 + H11 * u1 + H12 * u2;
+                        h2 += H02 * u0 + H12 * u1 + H22 * u2;
+                    }
+                }
+            }
+            acc0 += double(h0);
+            acc1 += double(h1);
+            acc2 += double(h2);
+        }
+    }
+    // Cartesian: grad_alpha = sum_beta C_{beta alpha} acc_beta
+    double gx = cm[0] * acc0 + cm[3] * acc1 + cm[6] * acc2;
+    double gy = cm[1] * acc0 + cm[4] * acc1 + cm[7] * acc2;
+    double gz = cm[2] * acc0 + cm[5] * acc1 + cm[8] * acc2;
+    // ---- real space: sum_j sum_l dA_ab/dr_c (p_ia q_jb + p_ja q_ib)
+    {
+        const double xi = a.pos[3 * i], yi = a.pos[3 * i + 1], zi = a.pos[3 * i + 2];
+        const double *cell = a.g.cell;
+        for (int nb = a.row[i]; nb < a.row[i + 1]; ++nb) {
+            const int j = a.col[nb];
+            const int sh = a.shift[nb];
+            const double n1 = double((sh & 255) - 128), n2 = double(((sh >> 8) & 255) - 128),
+                         n3 = double(((sh >> 16) & 255) - 128);
+            const double rx = xi - a.pos[3 * j] - (n1 * cell[0] + n2 * cell[3] + n3 * cell[6]);
+            const double ry = yi - a.pos[3 * j + 1] - (n1 * cell[1] + n2 * cell[4] + n3 * cell[7]);
+            const double rz = zi - a.pos[3 * j + 2] - (n1 * cell[2] + n2 * cell[5] + n3 * cell[8]);
+            double dA[18];
+            pair_tensor_grad_impl(rx, ry, rz, a.rvdw[i] + a.rvdw[j], a.beta, a.r_cut, a.damp_cut, a.damp_beta,
+                                  a.damp_d, dA);
+            // symmetric M_ab = sum_l (p_ia q_jb + p_ja q_ib), folded for the (ab) pairs
+            double M[6] = {0, 0, 0, 0, 0, 0};
+            for (int l = lane; l < a.R; l += 32) {
+                T pi_[3], qi_[3], pj_[3], qj_[3];
+                for (int c = 0; c < 3; ++c) {
+                    pi_[c] = a.dpq[(size_t)(3 * i + c) * a.ld2 + 2 * l];
+                    qi_[c] = a.dpq[(size_t)(3 * i + c) * a.ld2 + 2 * l + 1];
+                    pj_[c] = a.dpq[(size_t)(3 * j + c) * a.ld2 + 2 * l];
+                    qj_[c] = a.dpq[(size_t)(3 * j + c) * a.ld2 + 2 * l + 1];
+                }
+                int o = 0;
+                for (int x = 0; x < 3; ++x)
+                    for (int y = x; y < 3; ++y) {
+                        double v = double(pi_[x] * qj_[y] + pj_[x] * qi_[y]);
+                        if (x != y) v += double(pi_[y] * qj_[x] + pj_[y] * qi_[x]);
+                        M[o++] += v;
+                    }
+            }
+            for (int ab = 0; ab < 6; ++ab) {
+                gx += dA[3 * ab] * M[ab];
+                gy += dA[3 * ab + 1] * M[ab];
+                gz += dA[3 * ab + 2] * M[ab];
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        gx += __shfl_down_sync(0xffffffffu, gx, off);
+        gy += __shfl_down_sync(0xffffffffu, gy, off);
+        gz += __shfl_down_sync(0xffffffffu, gz, off);
+    }
+    if (lane == 0) {
+        a.forces[3 * i] = -a.scale * gx;
+        a.forces[3 * i + 1] = -a.scale * gy;
+        a.forces[3 * i + 2] = -a.scale * gz;
+    }
+}
+
+template <class T> PrecData<T> &prec(mbd_system *s);
+template <> PrecData<double> &prec<double>(mbd_system *s) { return s->f64; }
+template <> PrecData<float> &prec<float>(mbd_system *s) { return s->f32; }
+
+}  // namespace
+
+template <class T>
+mbd_status launch_force_dipoles_t(mbd_system *s, const double *Y, const double *coef, const int *length, int R,
+                                  int ld, int m, T *dpq, int ld2) {
+    const int rows = 3 * s->N;
+    const size_t n = (size_t)rows * R;
+    k_force_dipoles<T><<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(rows, Y, coef, length, s->g_d.as<double>(),
+                                                                          R, ld, m, dpq, ld2);
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+template <class T>
+mbd_status launch_force_gather_t(mbd_system *s, const T *dpq, const T *mesh, int R, int ld2, double scale,
+                                 double *forces) {
+    PrecData<T> &P = prec<T>(s);
+    ForceArgs<T> a;
+    a.dpq = dpq;
+    a.mesh = mesh;
+    a.R = R;
+    a.ld2 = ld2;
+    a.g.N = s->N;
+    a.g.K1 = s->K[0];
+    a.g.K2 = s->K[1];
+    a.g.K3 = s->K[2];
+    a.g.p = s->p;
+    for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c) a.g.cmat[3 * b + c] = s->K[b] * s->recip[3 * b + c];
+    for (int k = 0; k < 9; ++k) a.g.cell[k] = s->cell[k];
+    a.top = s->top_d.as<int>();
+    a.w = P.w.template as<T>();
+    a.dw = P.dw.template as<T>();
+    a.d2w = P.d2w.template as<T>();
+    a.row = s->row_d.as<int>();
+    a.col = s->col_d.as<int>();
+    a.shift = s->shift_d.as<int>();
+    a.pos = s->pos_d.as<double>();
+    a.rvdw = s->rvdw_d.as<double>();
+    a.beta = s->ewald_beta;
+    a.r_cut = s->r_cut;
+    a.damp_cut = s->damp_cut;
+    a.damp_beta = s->damp_beta;
+    a.damp_d = s->damp_d;
+    a.scale = scale;
+    a.forces = forces;
+    k_force_gather<T><<<(s->N + kWarps - 1) / kWarps, kWarps * 32, 0, s->stream>>>(a);
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+template mbd_status launch_force_dipoles_t<double>(mbd_system *, const double *, const double *, const int *, int, int,
+                                                   int, double *, int);
+template mbd_status launch_force_dipoles_t<float>(mbd_system *, const double *, const double *, const int *, int, int,
+                                                  int, float *, int);
+template mbd_status launch_force_gather_t<double>(mbd_system *, const double *, const double *, int, int, double,
+                                                  double *);
+template mbd_status launch_force_gather_t<float>(mbd_system *, const float *, const float *, int, int, double,
+                                                 double *);
+
+}  // namespace mbd

@@ -1,0 +1,227 @@
+// Per-system setup kernels: real-space pair tensors, B-spline stencils and the
+// SPME influence function.  These run once per geometry (mbd_create_system,
+// mbd_update_positions), not per Lanczos step.
+#include "mbd_internal.cuh"
+
+#include <cmath>
+
+namespace mbd {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kSqrtPi = 1.77245385090551602730;
+
+// Real-space pair tensor of E^dir with the damping correction (Eq. fld_ewald):
+//   A(r) = [|r| < r_cut] (B1 I - B2 r r^T) - [|r| < damp_cut] (1 - s(|r|)) T(r)
+// with Smith's erfc-screened B1, B2 and the bare T(r) = (r^2 I - 3 r r^T)/r^5.
+// Computed in FP64 from positions and the image shift, stored in T.
+template <class T>
+__global__ void k_pair_tensors(int N, const double *__restrict__ pos, const double *__restrict__ rvdw,
+                               const int *__restrict__ row, const int *__restrict__ col,
+                               const int *__restrict__ shift, Geom g, double beta, double r_cut,
+                               double damp_cut, double damp_beta, double damp_d, T *__restrict__ A) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    for (int nb = row[i] + lane; nb < row[i + 1]; nb += 32) {
+        const int j = col[nb];
+        const int sh = shift[nb];
+        const double n1 = double((sh & 255) - 128), n2 = double(((sh >> 8) & 255) - 128),
+                     n3 = double(((sh >> 16) & 255) - 128);
+        const double rx = xi - pos[3 * j] - (n1 * g.cell[0] + n2 * g.cell[3] + n3 * g.cell[6]);
+        const double ry = yi - pos[3 * j + 1] - (n1 * g.cell[1] + n2 * g.cell[4] + n3 * g.cell[7]);
+        const double rz = zi - pos[3 * j + 2] - (n1 * g.cell[2] + n2 * g.cell[5] + n3 * g.cell[8]);
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        const double rho = sqrt(r2);
+        double c_id = 0.0, c_rr = 0.0;   // A = c_id I - c_rr r r^T
+        if (rho < r_cut) {
+            const double e = exp(-beta * beta * r2);
+            const double b0 = erfc(beta * rho) / rho;
+            const double b1 = (b0 + 2.0 * beta / kSqrtPi * e) / r2;
+            const double b2 = (3.0 * b1 + 4.0 * beta * beta * beta / kSqrtPi * e) / r2;
+            c_id += b1;
+            c_rr += b2;
+        }
+        if (rho < damp_cut) {
+            const double rsum = rvdw[i] + rvdw[j];
+            const double one_minus_s = 1.0 / (1.0 + exp(damp_d * (rho / (damp_beta * rsum) - 1.0)));
+            const double r5 = r2 * r2 * rho;
+            c_id -= one_minus_s * r2 / r5;
+            c_rr -= one_minus_s * 3.0 / r5;
+        }
+        T *a = A + 6 * (size_t)nb;
+        a[0] = T(c_id - c_rr * rx * rx);
+        a[1] = T(-c_rr * rx * ry);
+        a[2] = T(-c_rr * rx * rz);
+        a[3] = T(c_id - c_rr * ry * ry);
+        a[4] = T(-c_rr * ry * rz);
+        a[5] = T(c_id - c_rr * rz * rz);
+    }
+}
+
+// Cardinal B-spline values on the stencil of one coordinate (Eq. scaledfractional):
+// for x = frac(u) in [0,1), m[t] = M_p(x + t), dm[t] = M_p'(x + t), d2m[t] = M_p''(x + t),
+// t = 0..p-1, from M_2 by the recursion M_n(y) = (y M_{n-1}(y) + (n - y) M_{n-1}(y - 1)) / (n - 1);
+// M_n' = M_{n-1}(y) - M_{n-1}(y-1) and M_n'' = M_{n-2}(y) - 2 M_{n-2}(y-1) + M_{n-2}(y-2).
+__device__ void bspline_stencil(double x, int p, double *m, double *dm, double *d2m) {
+    double cur[kMaxOrder + 1], prev[kMaxOrder + 1], prev2[kMaxOrder + 1];
+    for (int t = 0; t <= kMaxOrder; ++t) cur[t] = prev[t] = prev2[t] = 0.0;
+    cur[0] = x;
+    cur[1] = 1.0 - x;   // M_2(x), M_2(x+1)
+    for (int n = 3; n <= p; ++n) {
+        for (int t = 0; t <= kMaxOrder; ++t) {
+            prev2[t] = prev[t];
+            prev[t] = cur[t];
+        }
+        for (int t = 0; t < n; ++t) {
+            const double y = x + t;
+            const double hi = (t < n - 1) ? prev[t] : 0.0;
+            const double lo = (t >= 1) ? prev[t - 1] : 0.0;
+            cur[t] = (y * hi + (double(n) - y) * lo) / double(n - 1);
+        }
+    }
+    // here cur = M_p, prev = M_{p-1}, prev2 = M_{p-2} (p >= 4)
+    for (int t = 0; t < p; ++t) {
+        m[t] = cur[t];
+        dm[t] = prev[t] - (t >= 1 ? prev[t - 1] : 0.0);
+        d2m[t] = prev2[t] - 2.0 * (t >= 1 ? prev2[t - 1] : 0.0) + (t >= 2 ? prev2[t - 2] : 0.0);
+    }
+}
+
+// Per atom and dimension: u = K a*.R wrapped to [0, K), top = floor(u) and the
+// stencil weights of mesh points top - t (mod K).
+template <class T>
+__global__ void k_splines(int N, const double *__restrict__ pos, Geom g, int *__restrict__ top,
+                          T *__restrict__ w, T *__restrict__ dw, T *__restrict__ d2w) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 3 * N) return;
+    const int i = idx / 3, a = idx % 3;
+    const int K = a == 0 ? g.K1 : (a == 1 ? g.K2 : g.K3);
+    // recip row a = cmat row a / K
+    const double u_raw = (g.cmat[3 * a] * pos[3 * i] + g.cmat[3 * a + 1] * pos[3 * i + 1] +
+                          g.cmat[3 * a + 2] * pos[3 * i + 2]);
+    double u = u_raw - floor(u_raw / K) * K;
+    if (u >= K) u -= K;
+    if (u < 0.0) u = 0.0;
+    int t0 = (int)floor(u);
+    if (t0 >= K) t0 = K - 1;
+    const double x = u - t0;
+    double m[kMaxOrder], dm[kMaxOrder], d2m[kMaxOrder];
+    bspline_stencil(x, g.p, m, dm, d2m);
+    top[idx] = t0;
+    for (int t = 0; t < g.p; ++t) {
+        w[(size_t)idx * g.p + t] = T(m[t]);
+        dw[(size_t)idx * g.p + t] = T(dm[t]);
+        d2w[(size_t)idx * g.p + t] = T(d2m[t]);
+    }
+}
+
+// G(m) = B(m) exp(-pi^2 |m|^2 / beta^2) / (pi V |m|^2), G(0) = 0 (tin-foil),
+// m = sum_alpha m_alpha a*_alpha with the folded index (m = k for k <= K/2,
+// else k - K), symmetrised with G(-m mod K).
+__device__ double influence_at(int k1, int k2, int k3, Geom g, const double *bm1, const double *bm2,
+                               const double *bm3, double beta, double vol) {
+    if (k1 == 0 && k2 == 0 && k3 == 0) return 0.0;
+    const int f1 = k1 <= g.K1 / 2 ? k1 : k1 - g.K1;
+    const int f2 = k2 <= g.K2 / 2 ? k2 : k2 - g.K2;
+    const int f3 = k3 <= g.K3 / 2 ? k3 : k3 - g.K3;
+    // a*_alpha = cmat row alpha / K_alpha
+    double mx = 0, my = 0, mz = 0;
+    const double c1 = double(f1) / g.K1, c2 = double(f2) / g.K2, c3 = double(f3) / g.K3;
+    mx = c1 * g.cmat[0] + c2 * g.cmat[3] + c3 * g.cmat[6];
+    my = c1 * g.cmat[1] + c2 * g.cmat[4] + c3 * g.cmat[7];
+    mz = c1 * g.cmat[2] + c2 * g.cmat[5] + c3 * g.cmat[8];
+    const double m2 = mx * mx + my * my + mz * mz;
+    return bm1[k1] * bm2[k2] * bm3[k3] * exp(-kPi * kPi * m2 / (beta * beta)) / (kPi * vol * m2);
+}
+
+template <class T>
+__global__ void k_influence(Geom g, const double *__restrict__ bmod, double beta, double vol, T *__restrict__ G) {
+    const size_t total = (size_t)g.K1 * g.K2 * g.K3;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int k3 = idx % g.K3;
+    const int k2 = (idx / g.K3) % g.K2;
+    const int k1 = idx / ((size_t)g.K2 * g.K3);
+    const double *bm1 = bmod, *bm2 = bmod + g.K1, *bm3 = bmod + g.K1 + g.K2;
+    const double gp = influence_at(k1, k2, k3, g, bm1, bm2, bm3, beta, vol);
+    const double gn = influence_at((g.K1 - k1) % g.K1, (g.K2 - k2) % g.K2, (g.K3 - k3) % g.K3, g, bm1, bm2,
+                                   bm3, beta, vol);
+    G[idx] = T(0.5 * (gp + gn));
+}
+
+Geom make_geom(const mbd_system *s) {
+    Geom g;
+    g.N = s->N;
+    g.K1 = s->K[0];
+    g.K2 = s->K[1];
+    g.K3 = s->K[2];
+    g.p = s->p;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) g.cmat[3 * b + a] = s->K[b] * s->recip[3 * b + a];
+    for (int k = 0; k < 9; ++k) g.cell[k] = s->cell[k];
+    return g;
+}
+
+template <class T> PrecData<T> &prec(mbd_system *s);
+template <> PrecData<double> &prec<double>(mbd_system *s) { return s->f64; }
+template <> PrecData<float> &prec<float>(mbd_system *s) { return s->f32; }
+
+}  // namespace
+
+template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st) {
+    PrecData<T> &P = prec<T>(s);
+    MBD_TRY(P.pairA.ensure(sizeof(T) * 6 * (size_t)(s->nnz > 0 ? s->nnz : 1)));
+    if (s->nnz == 0) return MBD_OK;
+    const Geom g = make_geom(s);
+    const int threads = 256;
+    const int blocks = (int)(((long long)s->N * 32 + threads - 1) / threads);
+    k_pair_tensors<T><<<blocks, threads, 0, st>>>(s->N, s->pos_d.as<double>(), s->rvdw_d.as<double>(),
+                                                  s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(), g,
+                                                  s->ewald_beta, s->r_cut, s->damp_cut, s->damp_beta, s->damp_d,
+                                                  P.pairA.template as<T>());
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+template <class T> mbd_status launch_splines(mbd_system *s, cudaStream_t st) {
+    PrecData<T> &P = prec<T>(s);
+    const size_t n = (size_t)s->N * 3 * s->p;
+    MBD_TRY(P.w.ensure(sizeof(T) * n));
+    MBD_TRY(P.dw.ensure(sizeof(T) * n));
+    MBD_TRY(P.d2w.ensure(sizeof(T) * n));
+    const Geom g = make_geom(s);
+    const int threads = 256;
+    k_splines<T><<<(3 * s->N + threads - 1) / threads, threads, 0, st>>>(
+        s->N, s->pos_d.as<double>(), g, s->top_d.as<int>(), P.w.template as<T>(), P.dw.template as<T>(), P.d2w.template as<T>());
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod_host, cudaStream_t st) {
+    PrecData<T> &P = prec<T>(s);
+    const size_t total = (size_t)s->K[0] * s->K[1] * s->K[2];
+    MBD_TRY(P.G.ensure(sizeof(T) * total));
+    DevBuf bm;
+    const size_t nb = (size_t)(s->K[0] + s->K[1] + s->K[2]);
+    MBD_TRY(bm.ensure(sizeof(double) * nb));
+    MBD_CUDA_TRY(cudaMemcpyAsync(bm.ptr, bmod_host, sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+    const Geom g = make_geom(s);
+    const int threads = 256;
+    k_influence<T><<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(g, bm.as<double>(), s->ewald_beta,
+                                                                                   s->volume, P.G.template as<T>());
+    MBD_LAUNCH_CHECK();
+    MBD_CUDA_TRY(cudaStreamSynchronize(st));   // bm is freed on return
+    return MBD_OK;
+}
+
+template mbd_status launch_pair_tensors<double>(mbd_system *, cudaStream_t);
+template mbd_status launch_pair_tensors<float>(mbd_system *, cudaStream_t);
+template mbd_status launch_splines<double>(mbd_system *, cudaStream_t);
+template mbd_status launch_splines<float>(mbd_system *, cudaStream_t);
+template mbd_status launch_influence<double>(mbd_system *, const double *, cudaStream_t);
+template mbd_status launch_influence<float>(mbd_system *, const double *, cudaStream_t);
+
+}  // namespace mbd

@@ -1,0 +1,216 @@
+// Internal declarations shared by the translation units of libmbd.
+//
+// Data layout on the device (probe-innermost, "ld" = padded probe count, even):
+//   Lanczos vectors (FP64)      [3N][ld]           row (3i + alpha), column = probe
+//   dipoles d, fields E (T)     [N][3][ld]         same indexing as above
+//   SPME mesh (T)               [K1][K2][K3][ld]   = complex [K1][K2][K3][ld/2]:
+//                               probes (2v, 2v+1) form the real/imaginary parts
+//                               of one complex vector; since the influence
+//                               function is real and even, one complex FFT
+//                               convolution serves two probes exactly.
+//   spline stencil (T)          w, dw [N][3][p]    M_p(frac(u) + t), M_p'(...), t = 0..p-1
+//                               for mesh points top - t (mod K) per dimension
+//   real-space pairs            CSR over atoms i: col j, packed image shift,
+//                               pair tensor A (6 unique entries xx xy xz yy yz zz)
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "mbd.h"
+
+namespace mbd {
+
+constexpr int kMaxSteps = 128;
+constexpr int kMaxOrder = 10;
+constexpr int kMaxRadixStages = 12;
+constexpr double kBreakdown = 1e-14;
+
+template <class T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// ---------------------------------------------------------------- errors
+void set_last_error(const char *where, cudaError_t e);
+#define MBD_CUDA_TRY(call)                                               \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) {                                         \
+            ::mbd::set_last_error(#call, e_);                            \
+            return e_ == cudaErrorMemoryAllocation ? MBD_ERR_OOM : MBD_ERR_CUDA; \
+        }                                                                \
+    } while (0)
+#define MBD_LAUNCH_CHECK() MBD_CUDA_TRY(cudaGetLastError())
+#define MBD_TRY(expr)                       \
+    do {                                    \
+        mbd_status s_ = (expr);             \
+        if (s_ != MBD_OK) return s_;        \
+    } while (0)
+
+// ---------------------------------------------------------------- device buffer
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    mbd_status ensure(size_t n);   // grow (contents not preserved)
+    void release();
+    template <class U> U *as() const { return static_cast<U *>(ptr); }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+};
+
+// ---------------------------------------------------------------- kernel argument blocks
+struct Geom {
+    int N;
+    int K1, K2, K3;
+    int p;
+    double cmat[9];     // C[beta*3+alpha] = K_beta a*_{beta, alpha} (du_beta / dR_alpha)
+    double cell[9];
+};
+
+template <class T> struct SplineView {
+    const int *top;     // [N][3] floor(u) in [0, K)
+    const T *w;         // [N][3][p]
+    const T *dw;        // [N][3][p]
+    const T *d2w;       // [N][3][p] (forces only)
+};
+
+struct BinView {
+    int nb1, nb2, nb3;      // bricks (= bins) per dimension
+    int bs1, bs2, bs3;      // brick edge (mesh points)
+    int nc1, nc2, nc3;      // candidate bins per dimension for one brick
+    const int *start;       // [nbins+1]
+    const int *atoms;       // [N] atoms sorted by bin
+};
+
+template <class T> struct PairView {
+    const int *row;     // [N+1]
+    const int *col;     // [nnz]
+    const int *shift;   // [nnz] packed (n1+128) | (n2+128)<<8 | (n3+128)<<16
+    const T *A;         // [nnz][6]
+};
+
+struct LanczosView {
+    double *Y;          // [m][3N][ld] basis (y* written by the prologue, y after the field kernel)
+    double *L;          // [3N][ld] l_k = C y_k
+    double *a;          // [m][ld]
+    double *b;          // [m][ld]  b[k] couples y_k and y_{k+1}
+    double *invb;       // [ld]     1/b for the current step (0 after breakdown)
+    int *length;        // [ld]     Krylov length per probe (m unless broken down)
+    double *partial;    // [nblk][ld] block partial sums
+    unsigned *counter;  // [nchunk] last-block counters (self-resetting)
+};
+
+// ---------------------------------------------------------------- per-system state
+struct SystemData;
+
+template <class T> struct PrecData {
+    DevBuf pairA;       // [nnz][6]
+    DevBuf w, dw, d2w;  // [N][3][p]
+    DevBuf G;           // [K1K2K3] influence function
+    DevBuf tw1, tw2, tw3;   // twiddles [K] complex per dimension
+    DevBuf d;           // dipoles [N][3][ld]
+    DevBuf mesh;        // [K1K2K3][ld]
+};
+
+struct FFTDim {
+    int K;
+    int nst;
+    int radix[kMaxRadixStages];
+};
+
+}  // namespace mbd
+
+struct mbd_system {
+    // parameters
+    int N;
+    double cell[9], recip[9], volume;
+    int K[3], p;
+    double ewald_beta, r_cut, damp_cut, damp_beta, damp_d;
+    int precision;
+    cudaStream_t stream;
+    double omega_sum;
+    mbd::FFTDim fft[3];
+    // host copies
+    std::vector<double> pos, alpha, omega, rvdw;
+    std::vector<int> h_row, h_col, h_shift;
+    // common device data
+    mbd::DevBuf pos_d, g_d, w2_d, rvdw_d;            // [N][3], [N], [N], [N]
+    mbd::DevBuf row_d, col_d, shift_d;              // CSR
+    mbd::DevBuf top_d;                              // [N][3]
+    mbd::DevBuf bin_start_d, bin_atoms_d, order_d;  // spread bins; field atom order
+    mbd::BinView bins;
+    long long nnz;
+    // precision-specific
+    mbd::PrecData<double> f64;
+    mbd::PrecData<float> f32;
+    // Lanczos workspace
+    mbd::DevBuf Y, L, a, b, invb, length, partial, counter, q, scal, status, work, work2;
+    mbd::DevBuf forces_acc;
+    // pinned host staging
+    double *host_scal = nullptr;
+    int *host_status = nullptr;
+};
+
+namespace mbd {
+
+// ---------------------------------------------------------------- launchers (kernels_*.cu)
+// setup
+template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st);
+template <class T> mbd_status launch_splines(mbd_system *s, cudaStream_t st);
+template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod_host, cudaStream_t st);
+
+// mesh stages
+template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, int R, int ld);
+template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld);   // in place
+enum FieldMode { kFieldOut = 0, kFieldApply = 1, kFieldLanczos = 2 };
+template <class T> struct FieldOut {
+    int mode;
+    int terms;
+    double *out;            // kFieldOut: E [3N][ld]; kFieldApply: y [3N][ld]
+    const double *xin;      // kFieldApply: x [3N][ld]
+    LanczosView lz;         // kFieldLanczos
+    int k;                  // Lanczos step
+};
+template <class T> mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
+                                           const FieldOut<T> &o);
+
+// Lanczos
+mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int m, uint64_t seed, int R, int ld,
+                             int rows, const double *g, void *dout, int dtype_bytes, int nblk);
+mbd_status launch_quadrature_t(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
+                               int *status, double *work, cudaStream_t st);
+mbd_status launch_inv_sqrt_t(const double *a, const double *b, const int *length, int R, int ld, int m, double *coef,
+                             int *status, double *work, cudaStream_t st);
+mbd_status launch_energy_reduce(const double *q, int R, int dim, double omega_sum, double *scal, cudaStream_t st);
+mbd_status launch_probes(uint64_t seed, int first, int R, int dim, double *v, cudaStream_t st);
+mbd_status launch_dense_step(const double *c, int dim, const LanczosView &lz, int k, int R, int ld, int nblk,
+                             cudaStream_t st);
+int field_blocks(int N);
+
+// layout helpers
+mbd_status launch_to_probe_major(const double *x, int nvec, int rows, double *xt, int ld, cudaStream_t st);
+mbd_status launch_from_probe_major(const double *xt, int nvec, int rows, int ld, double *x, cudaStream_t st);
+template <class T> mbd_status launch_cast_rows(const double *x, T *y, size_t n, cudaStream_t st);
+template <class T> mbd_status launch_mesh_out(const T *mesh, int nvec, size_t npts, int ld, double *out,
+                                              cudaStream_t st);
+template <class T> mbd_status launch_mesh_in(const double *in, int nvec, size_t npts, int ld, T *mesh,
+                                             cudaStream_t st);
+
+// forces
+template <class T>
+mbd_status launch_force_dipoles_t(mbd_system *s, const double *Y, const double *coef, const int *length, int R,
+                                  int ld, int m, T *dpq, int ld2);
+template <class T>
+mbd_status launch_force_gather_t(mbd_system *s, const T *dpq, const T *mesh, int R, int ld2, double scale,
+                                 double *forces);
+
+// misc
+int probe_ld(int R);
+
+}  // namespace mbd

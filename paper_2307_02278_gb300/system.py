@@ -1,0 +1,173 @@
+"""Python binding of libmbd: the calls of include/mbd.h with the same names.
+
+PyTorch supplies device memory and the stream; every step of the method runs
+in the library's CUDA kernels.  Vectors cross the boundary as FP64 CUDA tensors
+of layout [nvec][N][3] (or [nvec][3N]).
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_void_p
+
+import numpy as np
+import torch
+
+from ._abi import (MBD_FP64, MBD_MIXED, MBD_TERM_ALL, Info, SystemDesc, check, lib)
+
+PRECISIONS = {"fp64": MBD_FP64, "mixed": MBD_MIXED}
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(c_double))
+
+
+def _cuda_f64(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    return t.contiguous()
+
+
+class MBDSystem:
+    """One periodic system on the GPU (mbd_create_system)."""
+
+    def __init__(self, cell, pos, alpha, omega, r_vdw, *, damp_beta=0.83, damp_d=6.0, ewald_beta=0.35,
+                 r_cut=10.0, damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64", stream=None):
+        self._handle = None
+        self.n_atoms = int(np.asarray(pos).shape[0])
+        self._pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        self._alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+        self._omega = np.ascontiguousarray(omega, dtype=np.float64)
+        self._rvdw = np.ascontiguousarray(r_vdw, dtype=np.float64)
+        d = SystemDesc()
+        d.n_atoms = self.n_atoms
+        d.cell[:] = [float(x) for x in np.asarray(cell, dtype=np.float64).ravel()]
+        d.pos = _dptr(self._pos)
+        d.alpha = _dptr(self._alpha)
+        d.omega = _dptr(self._omega)
+        d.r_vdw = _dptr(self._rvdw)
+        d.damp_beta, d.damp_d, d.ewald_beta = float(damp_beta), float(damp_d), float(ewald_beta)
+        d.r_cut, d.damp_cut = float(r_cut), float(damp_cut)
+        d.mesh[:] = [int(k) for k in mesh]
+        d.spline_order = int(spline_order)
+        d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.precision = precision
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sh = c_void_p(stream.cuda_stream if stream is not None else 0)
+        out = c_void_p()
+        check(lib().mbd_create_system(byref(d), sh, byref(out)), "mbd_create_system")
+        self._handle = out
+
+    @classmethod
+    def from_workload(cls, s, precision="fp64", **kw):
+        """Build from a workloads.System-like object (attributes of the same names)."""
+        return cls(s.cell, s.pos, s.alpha, s.omega, s.r_vdw, damp_beta=s.damp_beta, damp_d=s.damp_d,
+                   ewald_beta=s.ewald_beta, r_cut=s.r_cut, damp_cut=s.damp_cut, mesh=s.mesh,
+                   spline_order=s.spline_order, precision=precision, **kw)
+
+    # ------------------------------------------------------------------ lifetime
+    def close(self):
+        if self._handle is not None:
+            lib().mbd_destroy_system(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ calls
+    def update_positions(self, pos):
+        self._pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        check(lib().mbd_update_positions(self._handle, _dptr(self._pos)), "mbd_update_positions")
+
+    def info(self) -> dict:
+        inf = Info()
+        check(lib().mbd_get_info(self._handle, byref(inf)), "mbd_get_info")
+        return dict(n_atoms=inf.n_atoms, mesh=tuple(inf.mesh), n_pairs=inf.n_pairs,
+                    device_bytes=inf.device_bytes, precision=inf.precision)
+
+    def apply_C(self, x: torch.Tensor) -> torch.Tensor:
+        """y = C x for x of shape [nvec, 3N] (or [3N])."""
+        x = _cuda_f64(x, "x")
+        one = x.dim() == 1
+        xb = x.reshape(1 if one else x.shape[0], -1)
+        y = torch.empty_like(xb)
+        check(lib().mbd_apply_C(self._handle, xb.shape[0], xb.data_ptr(), y.data_ptr()), "mbd_apply_C")
+        return y[0] if one else y
+
+    def field(self, d: torch.Tensor, terms: int = MBD_TERM_ALL) -> torch.Tensor:
+        """E = T'^pbc d restricted to `terms`, d of shape [nvec, N, 3]."""
+        d = _cuda_f64(d, "d")
+        e = torch.empty_like(d)
+        check(lib().mbd_field(self._handle, d.shape[0], d.data_ptr(), e.data_ptr(), int(terms)), "mbd_field")
+        return e
+
+    def spread(self, d: torch.Tensor, mesh) -> torch.Tensor:
+        d = _cuda_f64(d, "d")
+        out = torch.empty((d.shape[0],) + tuple(mesh), dtype=torch.float64, device=d.device)
+        check(lib().mbd_spread(self._handle, d.shape[0], d.data_ptr(), out.data_ptr()), "mbd_spread")
+        return out
+
+    def convolve(self, q: torch.Tensor) -> torch.Tensor:
+        q = _cuda_f64(q, "mesh")
+        out = torch.empty_like(q)
+        check(lib().mbd_convolve(self._handle, q.shape[0], q.data_ptr(), out.data_ptr()), "mbd_convolve")
+        return out
+
+    def lanczos_energy(self, n_probes: int, n_steps: int, seed: int, details: bool = False):
+        """E_MBD by stochastic Lanczos quadrature; with details also the trace,
+        the per-probe quadratures q [R] and the tridiagonals a, b [R, m]."""
+        e = c_double()
+        tr = c_double()
+        q = np.zeros(n_probes) if details else None
+        ab = np.zeros((n_probes, 2, n_steps)) if details else None
+        check(lib().mbd_lanczos_energy(self._handle, n_probes, n_steps, seed, byref(e), byref(tr),
+                                       _dptr(q) if details else None, _dptr(ab) if details else None),
+              "mbd_lanczos_energy")
+        if not details:
+            return e.value
+        return e.value, dict(trace=tr.value, q=q, a=ab[:, 0], b=ab[:, 1])
+
+    def energy_forces(self, n_probes: int, n_steps: int, seed: int, forces: torch.Tensor | None = None):
+        """(E_MBD, F) with F = -dE/dR as a CUDA float64 tensor [N, 3]."""
+        if forces is None:
+            forces = torch.empty((self.n_atoms, 3), dtype=torch.float64, device="cuda")
+        forces = _cuda_f64(forces, "forces")
+        e = c_double()
+        check(lib().mbd_energy_forces(self._handle, n_probes, n_steps, seed, byref(e), forces.data_ptr()),
+              "mbd_energy_forces")
+        return e.value, forces
+
+
+def generate_probes(seed: int, n_probes: int, dim: int, first: int = 0) -> torch.Tensor:
+    v = torch.empty((n_probes, dim), dtype=torch.float64, device="cuda")
+    check(lib().mbd_generate_probes(seed, first, n_probes, dim, v.data_ptr()), "mbd_generate_probes")
+    return v
+
+
+def tridiag_quadrature(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    q = np.zeros(a.shape[0])
+    check(lib().mbd_tridiag_quadrature(a.shape[0], a.shape[1], _dptr(a), _dptr(b), _dptr(q)),
+          "mbd_tridiag_quadrature")
+    return q
+
+
+def lanczos_energy_dense(c: torch.Tensor, omega_sum: float, n_probes: int, n_steps: int, seed: int):
+    c = _cuda_f64(c, "C")
+    e = c_double()
+    q = np.zeros(n_probes)
+    ab = np.zeros((n_probes, 2, n_steps))
+    check(lib().mbd_lanczos_energy_dense(c.shape[0], c.data_ptr(), float(omega_sum), n_probes, n_steps, seed,
+                                         byref(e), _dptr(q), _dptr(ab)), "mbd_lanczos_energy_dense")
+    return e.value, dict(q=q, a=ab[:, 0], b=ab[:, 1])
