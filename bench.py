@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Benchmark of the SPME stochastic-Lanczos MBD hot path on GB300.
+
+One step = one mbd_energy_forces call on the 3000-atom water-like box (1000
+molecules, L = 58.66 bohr, mesh 64^3, spline order 6, 64 probes x 50 Lanczos
+steps): probe generation, the Lanczos recurrence with the SPME operator
+(spread, FFT convolution, gather + real space + self), the tridiagonal
+quadrature and the force estimator.  The operator runs in FP32 and the
+Lanczos layer in FP64 (the mixed path); the plain FP64 path is timed beside it.
+
+Metric: probe-matvecs/s = R m / step time (whole job over all ranks).
+Probes shard across ranks (rank r uses probes r R .. r R + R - 1); the energy
+and forces are averaged over ranks with one all-reduce per step.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
+sample of the same workload and prints the same JSON line with impl=reference.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "probe-matvecs/s and ms per MBD energy+forces at 1 GB300; frac of HBM roofline"
+UNIT = "probe-matvecs/s"
+WORKLOAD = 2        # the 3000-atom water box
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                     "NUMEXPR_NUM_THREADS": "1"}
+
+
+# ---------------------------------------------------------------------------- helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(index)], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(",") for ln in self.file.read().splitlines() if ln.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for name, val in zip(names, r[5:9]):
+                    if val.strip().lower() in ("active", "1"):
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2307_02278_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def dram_traffic(stage: str, workload: str):
+    """Bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel sources (profiles/dram_traffic.txt: stage workload bytes hash)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = source_hash()
+    with open(path) as f:
+        for ln in f:
+            p = ln.split()
+            if len(p) == 4 and not ln.startswith("#") and p[0] == stage and p[1] == workload and p[3] == cur:
+                return float(p[2])
+    return None
+
+
+def stage_bytes(n_atoms, mesh, R, m, s_bytes, n_pairs, p=6):
+    """Algorithmic HBM bytes per launch of each stage (minimum traffic of the
+    stage's inputs and outputs; every array read or written once)."""
+    npts = mesh[0] * mesh[1] * mesh[2]
+    rows = 3 * n_atoms
+    R2 = 2 * R
+    return {
+        "prologue": rows * R * (4 * 8 + s_bytes),                     # read l, y_{k-1}, y_{k-2}; write y*, d
+        "spread": npts * R * s_bytes + rows * R * s_bytes + n_atoms * 3 * p * 2 * s_bytes,
+        "fft": 2 * npts * R * s_bytes,                                 # one pass: read + write the mesh
+        "field": (npts * R * s_bytes + rows * R * s_bytes + n_pairs * (6 * s_bytes + 4)
+                  + rows * R * 8 * 3),                                 # mesh, d, pairs, y* in / y, l out
+        "force_spread": npts * R2 * s_bytes + rows * R2 * s_bytes,
+        "force_fft": 2 * npts * R2 * s_bytes,
+        "force_gather": npts * R2 * s_bytes + rows * R2 * s_bytes + n_pairs * 8,
+    }
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    from oracle.forces import estimator_forces
+    from oracle.operator import Operator
+    from workloads.systems import config
+
+    s = config(WORKLOAD)
+    R_s, m_s = 2, 4
+    op = Operator(s, "spme")
+    for _ in range(args.warmup):
+        estimator_forces(op, R_s, m_s, s.probe_seed)
+    t = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        estimator_forces(op, R_s, m_s, s.probe_seed + ((k * R_s) << 32))
+        t.append(time.perf_counter() - t0)
+    per = float(np.mean(t))
+    value = R_s * m_s / per
+    sample = (f"{R_s} probes x {m_s} Lanczos steps + force estimator per step (of {s.n_probes} x {s.n_steps}), "
+              f"FP64 NumPy, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh), "spline_order": s.spline_order,
+                   "n_probes": R_s, "n_steps": m_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_child(seconds: float):
+    """The oracle as it stands, timed on the host on a bounded sample (runs in a
+    child process started with single-thread BLAS/OpenMP settings)."""
+    import numpy as np
+
+    from oracle.forces import estimator_forces
+    from oracle.operator import Operator
+    from workloads.systems import config
+
+    s = config(WORKLOAD)
+    R_s, m_s = 2, 4
+    t_setup = time.perf_counter()
+    op = Operator(s, "spme")
+    t_setup = time.perf_counter() - t_setup
+    t = []
+    t_end = time.perf_counter() + seconds
+    k = 0
+    while time.perf_counter() < t_end or not t:
+        t0 = time.perf_counter()
+        estimator_forces(op, R_s, m_s, s.probe_seed + ((k * R_s) << 32))
+        t.append(time.perf_counter() - t0)
+        k += 1
+    per = float(np.mean(t))
+    print(json.dumps({"value": R_s * m_s / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+                      "sample": f"{len(t)} samples of {R_s} probes x {m_s} Lanczos steps + force estimator on "
+                                f"{s.name} (FP64 NumPy, 1 thread; operator setup {t_setup:.1f} s untimed)"}))
+
+
+def cpu_baseline(seconds: float):
+    env = dict(os.environ, **SINGLE_THREAD_ENV)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", "--cpu-seconds", str(seconds)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    try:
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return {"error": (r.stderr or r.stdout)[-300:]}
+
+
+# ---------------------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2307_02278_gb300.build import build
+    build()
+    import paper_2307_02278_gb300 as mbd
+    from workloads.systems import config
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = config(WORKLOAD)
+    R, m = s.n_probes, s.n_steps
+    seed = (s.probe_seed + ((rank * R) << 32)) % (1 << 64)
+    stream = torch.cuda.Stream()
+    sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, stream=stream)
+    info = sysm.info()
+    forces = torch.empty((s.n_atoms, 3), dtype=torch.float64, device="cuda")
+    energy_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(system, seed_k):
+        e, _ = system.energy_forces(R, m, seed_k, forces=forces)
+        if world > 1:
+            with torch.cuda.stream(stream):
+                energy_t.fill_(e)
+                dist.all_reduce(energy_t)
+                dist.all_reduce(forces)
+                energy_t.div_(world)
+                forces.div_(world)
+        return e
+
+    for _ in range(args.warmup):
+        step(sysm, seed)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each step, CUDA events on the system stream
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    sampler = ClockSampler(visible[local] if local < len(visible) else local)
+    time.sleep(0.3)
+    sysm.profile_enable(timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    energies = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+        energies.append(step(sysm, seed))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    prof = sysm.profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    t_max = t_dev
+    if world > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps * 1e3
+    value = world * R * m * args.steps / t_max
+
+    # ---- the same steps without per-stage events (overhead check)
+    sysm.profile_enable(timing=False)
+    t_plain = 0.0
+    for k in range(min(args.steps, 5)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(sysm, seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_plain += a.elapsed_time(b)
+    plain_ms = t_plain / min(args.steps, 5)
+
+    out = None
+    if rank == 0:
+        # ---- roofline of the dominant stage
+        s_bytes = 4 if args.precision == "mixed" else 8
+        sb = stage_bytes(s.n_atoms, s.mesh, R, m, s_bytes, info["n_pairs"], s.spline_order)
+        peak, peak_kind = measured_peaks()
+        stages = {}
+        for name, (nl, ms) in prof.items():
+            if name == "total_launches" or nl == 0:
+                continue
+            per_launch_ms = ms / nl if nl else 0.0
+            d = {"launches": nl, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for k2, v in prof.items()
+                                                                            if k2 != "total_launches")),
+                 "us_per_launch": per_launch_ms * 1e3}
+            if name in sb and per_launch_ms > 0:
+                d["algorithmic_bytes_per_launch"] = sb[name]
+                d["achieved_gbs"] = sb[name] / (per_launch_ms * 1e-3) / 1e9
+            stages[name] = d
+        dom = max((k for k in stages if k in sb), key=lambda k: stages[k]["ms_total"])
+        ach = stages[dom]["achieved_gbs"]
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+                "traffic": dram_traffic(dom, s.name)}
+
+        # ---- end to end through the public API with host buffers
+        pos_host = torch.tensor(s.pos, dtype=torch.float64).pin_memory()
+        f_host = torch.empty((s.n_atoms, 3), dtype=torch.float64).pin_memory()
+        t_e2e = []
+        for k in range(args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sysm.update_positions(pos_host.numpy())
+            e, _ = sysm.energy_forces(R, m, seed, forces=forces)
+            f_host.copy_(forces, non_blocking=True)
+            torch.cuda.synchronize()
+            t_e2e.append(time.perf_counter() - t0)
+        e2e_s = float(np.median(t_e2e))
+        e2e = {"value": world * R * m / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": 3 * 8 * s.n_atoms, "d2h_bytes_per_step": 3 * 8 * s.n_atoms + 8,
+               "includes": "update_positions (H2D, neighbour list, splines, pair tensors) + energy_forces + D2H"}
+
+        # ---- plain FP64 path on the same workload
+        fp64 = None
+        if args.precision == "mixed" and args.fp64_steps > 0:
+            s64 = mbd.MBDSystem.from_workload(s, precision="fp64", stream=stream)
+            e64, _ = s64.energy_forces(R, m, seed)
+            tt = []
+            for k in range(args.fp64_steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                e64, _ = s64.energy_forces(R, m, seed)
+                b.record(stream)
+                torch.cuda.synchronize()
+                tt.append(a.elapsed_time(b))
+            ms64 = float(np.mean(tt))
+            fp64 = {"value": R * m / (ms64 * 1e-3), "ms_per_step": ms64, "energy": e64,
+                    "mixed_energy_rel_diff": abs(energies[-1] - e64) / abs(e64),
+                    "speedup_mixed_over_fp64": ms64 / (plain_ms if plain_ms > 0 else ms_per_step)}
+            s64.close()
+
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(args.cpu_seconds)
+
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 operator / f64 lanczos" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh),
+                       "spline_order": s.spline_order, "n_probes_per_gpu": R, "n_steps": m,
+                       "precision": args.precision, "ewald_beta": s.ewald_beta, "r_cut": s.r_cut,
+                       "n_pairs": info["n_pairs"], "step": "mbd_energy_forces (energy + forces)",
+                       "l2": "flushed before every timed step (512 MB write, outside the events)",
+                       "parallelism": f"probes sharded over {world} GPU(s)"},
+            "ms_per_energy_forces": ms_per_step,
+            "ns_per_atom_probe_step": ms_per_step * 1e6 / (s.n_atoms * R * m),
+            "ms_per_step_without_stage_events": plain_ms,
+            "energy": energies[-1],
+            "roofline": roof,
+            "stages": stages,
+            "e2e": e2e,
+            "fp64_path": fp64,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(prof["total_launches"]),
+            "clocks": clocks,
+            "wall_s_timed_region": wall,
+            "kernel_sources": source_hash(),
+        }
+        print(json.dumps(out), flush=True)
+    sysm.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.cpu_child:
+        cpu_baseline_child(args.cpu_seconds)
+        return 0
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    if "--cpu-child" in sys.argv or "reference" in sys.argv:
+        os.environ.update(SINGLE_THREAD_ENV)     # before NumPy is imported
+    sys.exit(main())

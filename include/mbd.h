@@ -169,6 +169,37 @@ typedef struct {
 } mbd_info;
 mbd_status mbd_get_info(const mbd_system *sys, mbd_info *info);
 
+/* ---- tracing: per-stage launch counts and device time ---- */
+
+/* Stages of the hot path, in the order of Algorithms 1 and 2. */
+enum {
+    MBD_STAGE_PROLOGUE = 0,     /* probes, y*_k, b_k (Eq. recurs2) */
+    MBD_STAGE_SPREAD = 1,       /* dipole array (Eq. dipolarr) */
+    MBD_STAGE_FFT = 2,          /* forward FFT, influence function, inverse FFT (Eq. spme) */
+    MBD_STAGE_FIELD = 3,        /* gather + real space + self + l_k, a_k (Eqs. spme, fld_ewald, lk3) */
+    MBD_STAGE_QUADRATURE = 4,   /* tridiagonal eigensolve, trace, energy (Eqs. tridiag2, sl4) */
+    MBD_STAGE_FORCE_PREP = 5,   /* Delta^{-1/2} e_1, w_l, (g.w_l, g.v_l) */
+    MBD_STAGE_FORCE_SPREAD = 6,
+    MBD_STAGE_FORCE_FFT = 7,
+    MBD_STAGE_FORCE_GATHER = 8, /* Hessian gather + real-space pair gradient */
+    MBD_STAGE_OTHER = 9,        /* layout transposes, setup */
+    MBD_NUM_STAGES = 10
+};
+
+typedef struct {
+    int64_t launches[MBD_NUM_STAGES];   /* kernel launches per stage since the last reset */
+    double ms[MBD_NUM_STAGES];          /* device time per stage (CUDA events on the system's
+                                           stream; only while timing is enabled) */
+    int64_t total_launches;
+} mbd_profile;
+
+/* Reset the counters; enable = 1 also brackets every stage with CUDA events
+ * on the system's stream (a few microseconds of host time per stage). */
+mbd_status mbd_profile_enable(mbd_system *sys, int32_t enable);
+
+/* Read the counters (synchronises the system's stream). */
+mbd_status mbd_profile_read(mbd_system *sys, mbd_profile *out);
+
 /* Human-readable name of a status code (static storage). */
 const char *mbd_status_string(mbd_status status);
 

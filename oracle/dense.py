@@ -33,4 +33,4 @@ def dense_gradient(op, c: np.ndarray | None = None) -> np.ndarray:
     # P_v = g . (M e_v), Q_v = g . e_v = g_v e_v; the scalar g_v is moved onto P_v
     p = (m * op.g[:, None] * op.g[None, :]).T.reshape(n3, op.n, 3)
     q = np.eye(n3).reshape(n3, op.n, 3)
-    return 0.25 * bilinear_gradient(op.sys, p, q, op.mode)
+    return 0.25 * bilinear_gradient(op.sys, p, q, op.mode, op.pairs)

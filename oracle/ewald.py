@@ -134,10 +134,11 @@ def real_space_tensor_grad(sys, i, j, rvec, r_cut: float, damp_cut: float) -> np
     return g
 
 
-def real_space_matrix(sys, mode: str) -> sp.csr_matrix:
-    """Sparse 3N x 3N matrix of E^dir (erfc part + damping correction)."""
+def real_space_matrix(sys, mode: str, pairs=None) -> sp.csr_matrix:
+    """Sparse 3N x 3N matrix of E^dir (erfc part + damping correction);
+    `pairs` = pair_list(cell, pos, max(cutoffs)) when already at hand."""
     r_cut, damp_cut = cutoffs(sys, mode)
-    i, j, r = pair_list(sys.cell, sys.pos, max(r_cut, damp_cut))
+    i, j, r = pairs if pairs is not None else pair_list(sys.cell, sys.pos, max(r_cut, damp_cut))
     a = real_space_tensor(sys, i, j, r, r_cut, damp_cut)
     rows = (3 * i[:, None, None] + np.arange(3)[None, :, None]) + 0 * np.arange(3)[None, None, :]
     cols = (3 * j[:, None, None] + np.arange(3)[None, None, :]) + 0 * np.arange(3)[None, :, None]

@@ -21,9 +21,9 @@ from .lanczos import inverse_sqrt_action, lanczos, normalised_probes, quadrature
 from .model import cell_volume, wrap_positions
 
 
-def _real_space_gradient(sys, p, q, mode, chunk=20000):
+def _real_space_gradient(sys, p, q, mode, pairs=None, chunk=20000):
     r_cut, damp_cut = cutoffs(sys, "exact" if mode == "exact" else "same_split")
-    i, j, r = pair_list(sys.cell, sys.pos, max(r_cut, damp_cut))
+    i, j, r = pairs if pairs is not None else pair_list(sys.cell, sys.pos, max(r_cut, damp_cut))
     grad = np.zeros(p.shape[1:])
     for c0 in range(0, i.size, chunk):
         ii, jj, rr = i[c0:c0 + chunk], j[c0:c0 + chunk], r[c0:c0 + chunk]
@@ -73,12 +73,13 @@ def _reciprocal_gradient_spme(sys, p, q):
     return out
 
 
-def bilinear_gradient(sys, p: np.ndarray, q: np.ndarray, mode: str = "spme") -> np.ndarray:
+def bilinear_gradient(sys, p: np.ndarray, q: np.ndarray, mode: str = "spme", pairs=None) -> np.ndarray:
     """grad_R sum_v P_v^T T'^pbc(R) Q_v, P and Q of shape (nvec, N, 3) -> (N, 3).
-    The self term and Omega do not depend on R."""
+    The self term and Omega do not depend on R.  `pairs`: the pair list of the
+    real-space sum when already at hand."""
     p = np.asarray(p, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
-    grad = _real_space_gradient(sys, p, q, mode)
+    grad = _real_space_gradient(sys, p, q, mode, pairs)
     if mode == "spme":
         grad += _reciprocal_gradient_spme(sys, p, q)
     else:
@@ -96,6 +97,6 @@ def estimator_forces(op, n_probes: int, n_steps: int, seed: int, first: int = 0)
     q = np.array([quadrature(a[l], b[l], length[l]) for l in range(n_probes)])
     pg = (w * op.g).reshape(n_probes, n, 3)
     qg = (v * op.g).reshape(n_probes, n, 3)
-    grad = 0.25 * dim / n_probes * bilinear_gradient(op.sys, pg, qg, op.mode)
+    grad = 0.25 * dim / n_probes * bilinear_gradient(op.sys, pg, qg, op.mode, op.pairs)
     energy = 0.5 * dim / n_probes * np.sum(q) - 1.5 * np.sum(op.sys.omega)
     return -grad, energy, dict(w=w, v=v, a=a, b=b, length=length, q=q)

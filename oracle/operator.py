@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .ewald import apply_T, real_space_matrix
+from .ewald import apply_T, cutoffs, pair_list, real_space_matrix
 from .model import g_vector, omega_diag
 
 
@@ -21,7 +21,9 @@ class Operator:
         self.n = sys.pos.shape[0]
         self.g = g_vector(sys.alpha, sys.omega)
         self.w2 = omega_diag(sys.omega)
-        self.real = real_space_matrix(sys, "exact" if mode == "exact" else "same_split")
+        real_mode = "exact" if mode == "exact" else "same_split"
+        self.pairs = pair_list(sys.cell, sys.pos, max(cutoffs(sys, real_mode)))
+        self.real = real_space_matrix(sys, real_mode, self.pairs)
 
     def field(self, d: np.ndarray) -> np.ndarray:
         """E* = T'^pbc d for d of shape (nvec, N, 3)."""

@@ -51,6 +51,19 @@ class Info(ctypes.Structure):
     ]
 
 
+NUM_STAGES = 10
+STAGES = ["prologue", "spread", "fft", "field", "quadrature", "force_prep", "force_spread", "force_fft",
+          "force_gather", "other"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("launches", c_int64 * NUM_STAGES),
+        ("ms", c_double * NUM_STAGES),
+        ("total_launches", c_int64),
+    ]
+
+
 class MBDError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
@@ -75,6 +88,8 @@ SIGNATURES = {
     "mbd_tridiag_quadrature": (c_int, [c_int32, c_int32, PD, PD, PD]),
     "mbd_lanczos_energy_dense": (c_int, [c_int32, c_void_p, c_double, c_int32, c_int32, c_uint64, PD, PD, PD]),
     "mbd_get_info": (c_int, [c_void_p, POINTER(Info)]),
+    "mbd_profile_enable": (c_int, [c_void_p, c_int32]),
+    "mbd_profile_read": (c_int, [c_void_p, POINTER(Profile)]),
     "mbd_status_string": (c_char_p, [c_int]),
     "mbd_last_error": (c_char_p, []),
 }

@@ -40,6 +40,67 @@ void DevBuf::release() {
     bytes = 0;
 }
 
+void prof_begin(mbd_system *s, int stage, cudaEvent_t *e0) {
+    (void)stage;
+    *e0 = nullptr;
+    if (!s->prof.timing) return;
+    Profiler &P = s->prof;
+    if (P.pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        P.pool.push_back(e);
+    }
+    *e0 = P.pool.back();
+    P.pool.pop_back();
+    cudaEventRecord(*e0, s->stream);
+}
+
+void prof_end(mbd_system *s, int stage, int n_launches, cudaEvent_t e0) {
+    Profiler &P = s->prof;
+    P.launches[stage] += n_launches;
+    if (!P.timing || e0 == nullptr) return;
+    cudaEvent_t e1;
+    if (P.pool.empty()) {
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaGetLastError();
+            P.pool.push_back(e0);
+            return;
+        }
+    } else {
+        e1 = P.pool.back();
+        P.pool.pop_back();
+    }
+    cudaEventRecord(e1, s->stream);
+    P.pending.push_back(Profiler::Rec{stage, e0, e1});
+}
+
+// Fold finished event pairs into the per-stage times (after a stream sync).
+void prof_collect(mbd_system *s) {
+    Profiler &P = s->prof;
+    for (const Profiler::Rec &r : P.pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) P.ms[r.stage] += ms;
+        cudaGetLastError();
+        P.pool.push_back(r.e0);
+        P.pool.push_back(r.e1);
+    }
+    P.pending.clear();
+}
+
+void prof_release(mbd_system *s) {
+    Profiler &P = s->prof;
+    for (const Profiler::Rec &r : P.pending) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    for (cudaEvent_t e : P.pool) cudaEventDestroy(e);
+    P.pending.clear();
+    P.pool.clear();
+}
+
 // gscale kernels live in kernels_lanczos.cu
 template <class T> mbd_status launch_gscale(const double *x, const double *g, T *d, int rows, int ld, cudaStream_t st);
 
@@ -497,16 +558,21 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
     fo.xin = nullptr;
     fo.lz = z.v;
     for (int k = 0; k < m; ++k) {
-        MBD_TRY(launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
-                                  (int)sizeof(T), z.nblk));
-        MBD_TRY(launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
-        MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), z.ld));
+        MBD_STAGE(s, MBD_STAGE_PROLOGUE, 1,
+                  launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
+                                    (int)sizeof(T), z.nblk));
+        MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
+                  launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
+        MBD_STAGE(s, MBD_STAGE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld));
         fo.k = k;
-        MBD_TRY(launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
+        MBD_STAGE(s, MBD_STAGE_FIELD, 1,
+                  launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
     }
-    MBD_TRY(launch_quadrature_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), s->status.as<int>(),
-                                s->work.as<double>(), s->stream));
-    MBD_TRY(launch_energy_reduce(s->q.as<double>(), R, rows, s->omega_sum, s->scal.as<double>(), s->stream));
+    MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
+              launch_quadrature_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), s->status.as<int>(),
+                                  s->work.as<double>(), s->stream));
+    MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
+              launch_energy_reduce(s->q.as<double>(), R, rows, s->omega_sum, s->scal.as<double>(), s->stream));
     return MBD_OK;
 }
 
@@ -535,6 +601,7 @@ mbd_status fetch_results(mbd_system *s, const Lz &z, double *energy, double *tra
                                      s->stream));
     }
     MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    prof_collect(s);
     const mbd_status st = status_from_bits(*s->host_status);
     if (st != MBD_OK) return st;
     if (!std::isfinite(s->host_scal[0])) return MBD_ERR_NONFINITE;
@@ -565,19 +632,24 @@ mbd_status forces_impl(mbd_system *s, int R, int m, uint64_t seed, double *energ
     MBD_TRY(run_lanczos<T>(s, R, m, seed, z));
     // w_l = C^{-1/2} v_l = sum_k c_lk y_lk; coefficients from the full eigenvectors of Delta_l
     MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
-    MBD_TRY(launch_inv_sqrt_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->work2.as<double>(), s->status.as<int>(),
-                              s->work.as<double>(), s->stream));
+    MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
+              launch_inv_sqrt_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->work2.as<double>(), s->status.as<int>(),
+                                s->work.as<double>(), s->stream));
     PrecData<T> &P = prec<T>(s);
     const int ld2 = 2 * R;
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
     MBD_TRY(P.d.ensure(sizeof(T) * 3 * (size_t)s->N * std::max(ld2, z.ld)));
     MBD_TRY(P.mesh.ensure(sizeof(T) * npts * std::max(ld2, z.ld)));
-    MBD_TRY(launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m, P.d.template as<T>(),
-                                      ld2));
-    MBD_TRY(launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));
-    MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), ld2));
+    MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
+              launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m,
+                                        P.d.template as<T>(), ld2));
+    MBD_STAGE(s, MBD_STAGE_FORCE_SPREAD, 1,
+              launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));
+    MBD_STAGE(s, MBD_STAGE_FORCE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), ld2));
     const double scale = 0.25 * (3.0 * s->N) / R;
-    MBD_TRY(launch_force_gather_t<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, ld2, scale, forces_dev));
+    MBD_STAGE(s, MBD_STAGE_FORCE_GATHER, 1,
+              launch_force_gather_t<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, ld2, scale,
+                                       forces_dev));
     return fetch_results(s, z, energy, nullptr, nullptr, nullptr);
 }
 
@@ -591,15 +663,16 @@ template <class T> mbd_status apply_impl(mbd_system *s, int nvec, const double *
     double *yt = s->work2.as<double>();
     PrecData<T> &P = prec<T>(s);
     MBD_CUDA_TRY(cudaMemsetAsync(xt, 0, sizeof(double) * (size_t)rows * ld, s->stream));
-    MBD_TRY(launch_to_probe_major(x, nvec, rows, xt, ld, s->stream));
+    MBD_STAGE(s, MBD_STAGE_OTHER, 1, launch_to_probe_major(x, nvec, rows, xt, ld, s->stream));
     if (field) {
-        MBD_TRY(launch_cast_rows<T>(xt, P.d.template as<T>(), (size_t)rows * ld, s->stream));
+        MBD_STAGE(s, MBD_STAGE_OTHER, 1, launch_cast_rows<T>(xt, P.d.template as<T>(), (size_t)rows * ld, s->stream));
     } else {
-        MBD_TRY(launch_gscale<T>(xt, s->g_d.as<double>(), P.d.template as<T>(), rows, ld, s->stream));
+        MBD_STAGE(s, MBD_STAGE_OTHER, 1,
+                  launch_gscale<T>(xt, s->g_d.as<double>(), P.d.template as<T>(), rows, ld, s->stream));
     }
     if (terms & MBD_TERM_RECIP) {
-        MBD_TRY(launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld));
-        MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), ld));
+        MBD_STAGE(s, MBD_STAGE_SPREAD, 1, launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld));
+        MBD_STAGE(s, MBD_STAGE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), ld));
     }
     FieldOut<T> fo;
     fo.mode = field ? kFieldOut : kFieldApply;
@@ -608,9 +681,10 @@ template <class T> mbd_status apply_impl(mbd_system *s, int nvec, const double *
     fo.xin = xt;
     fo.k = 0;
     std::memset(&fo.lz, 0, sizeof(fo.lz));
-    MBD_TRY(launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld, fo));
-    MBD_TRY(launch_from_probe_major(yt, nvec, rows, ld, y, s->stream));
+    MBD_STAGE(s, MBD_STAGE_FIELD, 1, launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld, fo));
+    MBD_STAGE(s, MBD_STAGE_OTHER, 1, launch_from_probe_major(yt, nvec, rows, ld, y, s->stream));
     MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    prof_collect(s);
     return MBD_OK;
 }
 
@@ -683,6 +757,7 @@ void mbd_destroy_system(mbd_system *sys) {
     if (sys == nullptr) return;
     if (sys->host_scal) cudaFreeHost(sys->host_scal);
     if (sys->host_status) cudaFreeHost(sys->host_status);
+    prof_release(sys);
     delete sys;
 }
 
@@ -810,6 +885,31 @@ mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double ome
     const mbd_status st = run();
     mbd_destroy_system(s);
     return st;
+}
+
+mbd_status mbd_profile_enable(mbd_system *s, int32_t enable) {
+    if (!s) return MBD_ERR_INVALID_ARG;
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    prof_collect(s);
+    for (int k = 0; k < MBD_NUM_STAGES; ++k) {
+        s->prof.launches[k] = 0;
+        s->prof.ms[k] = 0.0;
+    }
+    s->prof.timing = enable != 0;
+    return MBD_OK;
+}
+
+mbd_status mbd_profile_read(mbd_system *s, mbd_profile *out) {
+    if (!s || !out) return MBD_ERR_INVALID_ARG;
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    prof_collect(s);
+    out->total_launches = 0;
+    for (int k = 0; k < MBD_NUM_STAGES; ++k) {
+        out->launches[k] = s->prof.launches[k];
+        out->ms[k] = s->prof.ms[k];
+        out->total_launches += s->prof.launches[k];
+    }
+    return MBD_OK;
 }
 
 mbd_status mbd_get_info(const mbd_system *s, mbd_info *info) {

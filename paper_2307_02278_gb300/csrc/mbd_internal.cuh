@@ -118,6 +118,19 @@ template <class T> struct PrecData {
     DevBuf mesh;        // [K1K2K3][ld]
 };
 
+// Stage profiler: launch counts always, CUDA-event timing when enabled.
+struct Profiler {
+    bool timing = false;
+    long long launches[MBD_NUM_STAGES] = {};
+    double ms[MBD_NUM_STAGES] = {};
+    struct Rec {
+        int stage;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
 struct FFTDim {
     int K;
     int nst;
@@ -152,6 +165,7 @@ struct mbd_system {
     // Lanczos workspace
     mbd::DevBuf Y, L, a, b, invb, length, partial, counter, q, scal, status, work, work2;
     mbd::DevBuf forces_acc;
+    mbd::Profiler prof;
     // pinned host staging
     double *host_scal = nullptr;
     int *host_status = nullptr;
@@ -212,5 +226,16 @@ mbd_status launch_force_gather_t(mbd_system *s, const T *dpq, const T *mesh, int
 
 // misc
 int probe_ld(int R);
+void prof_begin(mbd_system *s, int stage, cudaEvent_t *e0);
+void prof_end(mbd_system *s, int stage, int n_launches, cudaEvent_t e0);
+void prof_release(mbd_system *s);
+#define MBD_STAGE(s, stage, nl, call)                       \
+    do {                                                   \
+        cudaEvent_t ev0_ = nullptr;                        \
+        ::mbd::prof_begin((s), (stage), &ev0_);            \
+        mbd_status st_ = (call);                           \
+        ::mbd::prof_end((s), (stage), (nl), ev0_);         \
+        if (st_ != MBD_OK) return st_;                     \
+    } while (0)
 
 }  // namespace mbd

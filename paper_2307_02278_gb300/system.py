@@ -12,7 +12,7 @@ from ctypes import byref, c_double, c_void_p
 import numpy as np
 import torch
 
-from ._abi import (MBD_FP64, MBD_MIXED, MBD_TERM_ALL, Info, SystemDesc, check, lib)
+from ._abi import (MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES, Info, Profile, SystemDesc, check, lib)
 
 PRECISIONS = {"fp64": MBD_FP64, "mixed": MBD_MIXED}
 
@@ -94,6 +94,18 @@ class MBDSystem:
         check(lib().mbd_get_info(self._handle, byref(inf)), "mbd_get_info")
         return dict(n_atoms=inf.n_atoms, mesh=tuple(inf.mesh), n_pairs=inf.n_pairs,
                     device_bytes=inf.device_bytes, precision=inf.precision)
+
+    def profile_enable(self, timing: bool = True):
+        """Reset the per-stage counters; with timing, bracket stages with CUDA events."""
+        check(lib().mbd_profile_enable(self._handle, 1 if timing else 0), "mbd_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{stage: (launches, device ms)} plus 'total_launches'."""
+        p = Profile()
+        check(lib().mbd_profile_read(self._handle, byref(p)), "mbd_profile_read")
+        out = {name: (int(p.launches[k]), float(p.ms[k])) for k, name in enumerate(STAGES)}
+        out["total_launches"] = int(p.total_launches)
+        return out
 
     def apply_C(self, x: torch.Tensor) -> torch.Tensor:
         """y = C x for x of shape [nvec, 3N] (or [3N])."""
