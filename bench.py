@@ -328,13 +328,14 @@ def run_ours(args, world, rank, local):
         sb = stage_bytes(s.n_atoms, s.mesh, R, m, s_bytes, info["n_pairs"], s.spline_order)
         peak, peak_kind = measured_peaks()
         stages = {}
-        for name, (nl, ms) in prof.items():
-            if name == "total_launches" or nl == 0:
+        stage_names = [k for k in prof if k != "total_launches"]
+        total_ms = sum(prof[k][1] for k in stage_names)
+        for name in stage_names:
+            nl, ms = prof[name]
+            if nl == 0:
                 continue
-            per_launch_ms = ms / nl if nl else 0.0
-            d = {"launches": nl, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for k2, v in prof.items()
-                                                                            if k2 != "total_launches")),
-                 "us_per_launch": per_launch_ms * 1e3}
+            per_launch_ms = ms / nl
+            d = {"launches": nl, "ms_total": ms, "share": ms / max(1e-12, total_ms), "us_per_launch": per_launch_ms * 1e3}
             if name in sb and per_launch_ms > 0:
                 d["algorithmic_bytes_per_launch"] = sb[name]
                 d["achieved_gbs"] = sb[name] / (per_launch_ms * 1e-3) / 1e9
