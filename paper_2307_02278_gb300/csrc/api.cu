@@ -385,6 +385,7 @@ template <class T> mbd_status setup_geometry(mbd_system *s) {
     MBD_TRY(launch_pair_tensors<T>(s, s->stream));
     MBD_TRY(launch_splines<T>(s, s->stream));
     MBD_TRY(build_bins(s));
+    MBD_TRY(build_spread_matrix<T>(s));
     MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return MBD_OK;
 }
@@ -522,7 +523,6 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     MBD_TRY(s->q.ensure(sizeof(double) * ld));
     MBD_TRY(s->scal.ensure(sizeof(double) * 16));
     MBD_TRY(s->status.ensure(sizeof(int) * 4));
-    MBD_TRY(s->work.ensure(sizeof(double) * (size_t)(2 * m + m * m) * R));
     MBD_CUDA_TRY(cudaMemsetAsync(s->a.ptr, 0, sizeof(double) * (size_t)m * ld, s->stream));
     MBD_CUDA_TRY(cudaMemsetAsync(s->b.ptr, 0, sizeof(double) * (size_t)m * ld, s->stream));
     MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
@@ -546,7 +546,7 @@ template <class T> mbd_status ensure_mesh(mbd_system *s, int ld) {
 }
 
 // Algorithm 1 with Algorithm 2 per step: m Lanczos steps for all R probes.
-template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t seed, Lz &z) {
+template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t seed, Lz &z, bool full = false) {
     const int rows = 3 * s->N;
     MBD_TRY(lanczos_workspace(s, R, m, rows, field_blocks(s->N), z));
     MBD_TRY(ensure_mesh<T>(s, z.ld));
@@ -568,9 +568,10 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
         MBD_STAGE(s, MBD_STAGE_FIELD, 1,
                   launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
     }
+    if (full) MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
-              launch_quadrature_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), s->status.as<int>(),
-                                  s->work.as<double>(), s->stream));
+              launch_tridiag(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(),
+                             full ? s->work2.as<double>() : nullptr, s->status.as<int>(), s->stream));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
               launch_energy_reduce(s->q.as<double>(), R, rows, s->omega_sum, s->scal.as<double>(), s->stream));
     return MBD_OK;
@@ -629,12 +630,8 @@ mbd_status energy_impl(mbd_system *s, int R, int m, uint64_t seed, double *energ
 template <class T>
 mbd_status forces_impl(mbd_system *s, int R, int m, uint64_t seed, double *energy, double *forces_dev) {
     Lz z;
-    MBD_TRY(run_lanczos<T>(s, R, m, seed, z));
-    // w_l = C^{-1/2} v_l = sum_k c_lk y_lk; coefficients from the full eigenvectors of Delta_l
-    MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
-    MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
-              launch_inv_sqrt_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->work2.as<double>(), s->status.as<int>(),
-                                s->work.as<double>(), s->stream));
+    // w_l = C^{-1/2} v_l = sum_k c_lk y_lk with c = Delta^{-1/2} e_1 from the quadrature kernel
+    MBD_TRY(run_lanczos<T>(s, R, m, seed, z, true));
     PrecData<T> &P = prec<T>(s);
     const int ld2 = 2 * R;
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
@@ -833,19 +830,18 @@ mbd_status mbd_tridiag_quadrature(int32_t R, int32_t m, const double *a_host, co
             b[(size_t)k * R + r] = b_host[(size_t)r * m + k];
         }
     }
-    DevBuf da, db, dl, dq, dst, dw;
+    DevBuf da, db, dl, dq, dst;
     MBD_TRY(da.ensure(sizeof(double) * a.size()));
     MBD_TRY(db.ensure(sizeof(double) * b.size()));
     MBD_TRY(dl.ensure(sizeof(int) * R));
     MBD_TRY(dq.ensure(sizeof(double) * R));
     MBD_TRY(dst.ensure(sizeof(int)));
-    MBD_TRY(dw.ensure(sizeof(double) * 3 * (size_t)m * R));
     MBD_CUDA_TRY(cudaMemcpy(da.ptr, a.data(), sizeof(double) * a.size(), cudaMemcpyHostToDevice));
     MBD_CUDA_TRY(cudaMemcpy(db.ptr, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice));
     MBD_CUDA_TRY(cudaMemcpy(dl.ptr, len.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
     MBD_CUDA_TRY(cudaMemset(dst.ptr, 0, sizeof(int)));
-    MBD_TRY(launch_quadrature_t(da.as<double>(), db.as<double>(), dl.as<int>(), R, R, m, dq.as<double>(),
-                                dst.as<int>(), dw.as<double>(), nullptr));
+    MBD_TRY(launch_tridiag(da.as<double>(), db.as<double>(), dl.as<int>(), R, R, m, dq.as<double>(), nullptr,
+                           dst.as<int>(), nullptr));
     int bits = 0;
     MBD_CUDA_TRY(cudaMemcpy(&bits, dst.ptr, sizeof(int), cudaMemcpyDeviceToHost));
     MBD_TRY(status_from_bits(bits));
@@ -877,8 +873,8 @@ mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double ome
                                       z.nblk));
             MBD_TRY(launch_dense_step(c_dev, dim, z.v, k, R, z.ld, z.nblk, s->stream));
         }
-        MBD_TRY(launch_quadrature_t(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), s->status.as<int>(),
-                                    s->work.as<double>(), s->stream));
+        MBD_TRY(launch_tridiag(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), nullptr,
+                               s->status.as<int>(), s->stream));
         MBD_TRY(launch_energy_reduce(s->q.as<double>(), R, dim, omega_sum, s->scal.as<double>(), s->stream));
         return fetch_results(s, z, energy, nullptr, q_host, ab_host);
     };

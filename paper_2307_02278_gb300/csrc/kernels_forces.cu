@@ -15,7 +15,6 @@ namespace mbd {
 namespace {
 
 constexpr int kWarps = 8;
-constexpr double kSqrtPi = 1.77245385090551602730;
 
 template <class T>
 __global__ void k_force_dipoles(int rows, const double *__restrict__ Y, const double *__restrict__ coef,
@@ -40,60 +39,11 @@ template <class T> struct ForceArgs {
     Geom g;
     const int *top;
     const T *w, *dw, *d2w;
-    const int *row, *col, *shift;
-    const double *pos, *rvdw;
-    double beta, r_cut, damp_cut, damp_beta, damp_d;
+    const int *row, *col;
+    const T *dA;         // [nnz][18] dA_ab/dr_c of the real-space pair tensor
     double scale;
     double *forces;      // [N][3] FP64
 };
-
-// dA_ab / dr_c for the real-space pair tensor (FP64):
-//   erfc part  -B2 (delta_ab r_c + delta_ac r_b + delta_bc r_a) + B3 r_a r_b r_c
-//   damping    -d/dr_c [(1 - s) T_ab] with T_ab = delta_ab/r^3 - 3 r_a r_b / r^5
-__device__ void pair_tensor_grad_impl(double rx, double ry, double rz, double rsum, double beta, double r_cut,
-                                      double damp_cut, double damp_beta, double damp_d, double out[18]) {
-    const double rv[3] = {rx, ry, rz};
-    const double r2 = rx * rx + ry * ry + rz * rz;
-    const double rho = sqrt(r2);
-    // A = c_id I - c_rr r r^T with radial c_id, c_rr; dA_ab/dr_c =
-    //   (c_id'/rho) r_c delta_ab - (c_rr'/rho) r_c r_a r_b - c_rr (delta_ac r_b + delta_bc r_a)
-    double cid_p = 0.0, crr = 0.0, crr_p = 0.0;   // c_id'/rho, c_rr, c_rr'/rho
-    if (rho < r_cut) {
-        const double e = exp(-beta * beta * r2);
-        const double b0 = erfc(beta * rho) / rho;
-        const double b1 = (b0 + 2.0 * beta / kSqrtPi * e) / r2;
-        const double b2 = (3.0 * b1 + 4.0 * beta * beta * beta / kSqrtPi * e) / r2;
-        const double b3 = (5.0 * b2 + 8.0 * beta * beta * beta * beta * beta / kSqrtPi * e) / r2;
-        // (1/r) dB_n/dr = -B_{n+1}
-        cid_p += -b2;
-        crr += b2;
-        crr_p += -b3;
-    }
-    if (rho < damp_cut) {
-        const double x = damp_d * (rho / (damp_beta * rsum) - 1.0);
-        const double oms = 1.0 / (1.0 + exp(x));          // 1 - s
-        const double s = 1.0 - oms;
-        const double dsdr = damp_d / (damp_beta * rsum) * s * oms;
-        const double r3 = r2 * rho, r5 = r3 * r2;
-        // subtract (1-s) T:  c_id -= oms / r^3,  c_rr -= 3 oms / r^5
-        // d/dr (oms / r^3) = -dsdr / r^3 - 3 oms / r^4 ;  d/dr (3 oms / r^5) = -3 dsdr / r^5 - 15 oms / r^6
-        cid_p -= (-dsdr / r3 - 3.0 * oms / (r3 * rho)) / rho;
-        crr -= 3.0 * oms / r5;
-        crr_p -= (-3.0 * dsdr / r5 - 15.0 * oms / (r5 * rho)) / rho;
-    }
-    int o = 0;
-    for (int ab = 0; ab < 6; ++ab) {
-        const int ia = ab < 3 ? 0 : (ab < 5 ? 1 : 2);
-        const int ib = ab < 3 ? ab : (ab < 5 ? ab - 2 : 2);
-        for (int c = 0; c < 3; ++c) {
-            double v = -crr_p * rv[c] * rv[ia] * rv[ib];
-            if (ia == ib) v += cid_p * rv[c];
-            if (ia == c) v -= crr * rv[ib];
-            if (ib == c) v -= crr * rv[ia];
-            out[o++] = v;
-        }
-    }
-}
 
 template <class T>
 __global__ void __launch_bounds__(kWarps * 32) k_force_gather(ForceArgs<T> a) {
@@ -155,23 +105,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_force_gather(ForceArgs<T> a) {
     double gx = cm[0] * acc0 + cm[3] * acc1 + cm[6] * acc2;
     double gy = cm[1] * acc0 + cm[4] * acc1 + cm[7] * acc2;
     double gz = cm[2] * acc0 + cm[5] * acc1 + cm[8] * acc2;
-    // ---- real space: sum_j sum_l dA_ab/dr_c (p_ia q_jb + p_ja q_ib)
+    // ---- real space: sum_j dA_ab/dr_c sum_l (p_ia q_jb + p_ja q_ib), dA precomputed per pair
     {
-        const double xi = a.pos[3 * i], yi = a.pos[3 * i + 1], zi = a.pos[3 * i + 2];
-        const double *cell = a.g.cell;
+        T g0 = T(0), g1 = T(0), g2 = T(0);
         for (int nb = a.row[i]; nb < a.row[i + 1]; ++nb) {
             const int j = a.col[nb];
-            const int sh = a.shift[nb];
-            const double n1 = double((sh & 255) - 128), n2 = double(((sh >> 8) & 255) - 128),
-                         n3 = double(((sh >> 16) & 255) - 128);
-            const double rx = xi - a.pos[3 * j] - (n1 * cell[0] + n2 * cell[3] + n3 * cell[6]);
-            const double ry = yi - a.pos[3 * j + 1] - (n1 * cell[1] + n2 * cell[4] + n3 * cell[7]);
-            const double rz = zi - a.pos[3 * j + 2] - (n1 * cell[2] + n2 * cell[5] + n3 * cell[8]);
-            double dA[18];
-            pair_tensor_grad_impl(rx, ry, rz, a.rvdw[i] + a.rvdw[j], a.beta, a.r_cut, a.damp_cut, a.damp_beta,
-                                  a.damp_d, dA);
-            // symmetric M_ab = sum_l (p_ia q_jb + p_ja q_ib), folded for the (ab) pairs
-            double M[6] = {0, 0, 0, 0, 0, 0};
+            T M[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
             for (int l = lane; l < a.R; l += 32) {
                 T pi_[3], qi_[3], pj_[3], qj_[3];
                 for (int c = 0; c < 3; ++c) {
@@ -183,17 +122,21 @@ __global__ void __launch_bounds__(kWarps * 32) k_force_gather(ForceArgs<T> a) {
                 int o = 0;
                 for (int x = 0; x < 3; ++x)
                     for (int y = x; y < 3; ++y) {
-                        double v = double(pi_[x] * qj_[y] + pj_[x] * qi_[y]);
-                        if (x != y) v += double(pi_[y] * qj_[x] + pj_[y] * qi_[x]);
+                        T v = pi_[x] * qj_[y] + pj_[x] * qi_[y];
+                        if (x != y) v += pi_[y] * qj_[x] + pj_[y] * qi_[x];
                         M[o++] += v;
                     }
             }
+            const T *dA = a.dA + 18 * (size_t)nb;
             for (int ab = 0; ab < 6; ++ab) {
-                gx += dA[3 * ab] * M[ab];
-                gy += dA[3 * ab + 1] * M[ab];
-                gz += dA[3 * ab + 2] * M[ab];
+                g0 += dA[3 * ab] * M[ab];
+                g1 += dA[3 * ab + 1] * M[ab];
+                g2 += dA[3 * ab + 2] * M[ab];
             }
         }
+        gx += double(g0);
+        gy += double(g1);
+        gz += double(g2);
     }
     for (int off = 16; off > 0; off >>= 1) {
         gx += __shfl_down_sync(0xffffffffu, gx, off);
@@ -247,14 +190,7 @@ mbd_status launch_force_gather_t(mbd_system *s, const T *dpq, const T *mesh, int
     a.d2w = P.d2w.template as<T>();
     a.row = s->row_d.as<int>();
     a.col = s->col_d.as<int>();
-    a.shift = s->shift_d.as<int>();
-    a.pos = s->pos_d.as<double>();
-    a.rvdw = s->rvdw_d.as<double>();
-    a.beta = s->ewald_beta;
-    a.r_cut = s->r_cut;
-    a.damp_cut = s->damp_cut;
-    a.damp_beta = s->damp_beta;
-    a.damp_d = s->damp_d;
+    a.dA = P.pairdA.template as<T>();
     a.scale = scale;
     a.forces = forces;
     k_force_gather<T><<<(s->N + kWarps - 1) / kWarps, kWarps * 32, 0, s->stream>>>(a);

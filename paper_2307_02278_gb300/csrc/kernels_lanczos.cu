@@ -90,132 +90,145 @@ __global__ void __launch_bounds__(256) k_prologue(LanczosView lz, int k, int m, 
     }
 }
 
-// Implicit QL with Wilkinson shifts on a symmetric tridiagonal (diagonal d,
-// sub-diagonal e; Bowdler, Martin, Reinsch & Wilkinson 1968).  Accumulates the
-// plane rotations into the rows of Z selected by nz (nz = 1: the first row
-// only, which is all the Gauss weights U_1k^2 need; Golub & Welsch 1969).
-// Arrays are strided by `st` (probe-innermost scratch).  Returns false if an
-// eigenvalue needs more than 60 sweeps.
-__device__ bool ql_implicit(double *d, double *e, double *Z, int n, int nz, size_t st) {
+// Gauss quadrature of one probe's tridiagonal Delta (Eqs. tridiag2, sl3): a
+// warp per probe.  Implicit QL with Wilkinson shifts (Bowdler, Martin, Reinsch
+// & Wilkinson 1968): lane 0 runs the scalar chain of each sweep in shared
+// memory and records the plane rotations; then every lane applies them to its
+// rows of U (initially I).  The Gauss weights are U_1k^2 (Golub & Welsch
+// 1969), so without FULL only row 1 of U is kept.  With FULL the whole U is
+// kept and c = Delta^{-1/2} e_1 = U diag(theta^{-1/2}) U^T e_1 is returned as
+// well (w = C^{-1/2} v = sum_k c_k y_k for the force estimator).
+// status bit 1: a Ritz value <= 0; bit 2: a sweep limit hit; bit 4: NaN/Inf.
+template <bool FULL>
+__global__ void __launch_bounds__(32) k_tridiag(const double *__restrict__ a, const double *__restrict__ b,
+                                                const int *__restrict__ length, int R, int ld, int m,
+                                                double *__restrict__ q, double *__restrict__ coef,
+                                                int *__restrict__ status) {
+    extern __shared__ double sm[];
+    const int r = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (r >= R) return;
+    const int n = length ? length[r] : m;
+    const int zs = n + 1;                   // padded row stride of U (bank-conflict free)
+    double *d = sm, *e = sm + m, *cs = sm + 2 * m, *sn = sm + 3 * m, *Z = sm + 4 * m;
+    __shared__ int s_nrot, s_bad;
+    bool finite = true;
+    for (int k = lane; k < n; k += 32) {
+        d[k] = a[(size_t)k * ld + r];
+        e[k] = (k < n - 1) ? b[(size_t)k * ld + r] : 0.0;
+        finite = finite && isfinite(d[k]) && isfinite(e[k]);
+    }
+    const int nz = FULL ? n : 1;
+    for (int row = lane; row < nz; row += 32)
+        for (int col = 0; col < n; ++col) Z[row * zs + col] = (row == col) ? 1.0 : 0.0;
+    if (lane == 0) s_bad = 0;
+    finite = __all_sync(0xffffffffu, finite);
+    __syncwarp();
+    if (!finite) {
+        if (lane == 0) {
+            atomicOr(status, 4);
+            q[r] = 0.0;
+        }
+        if (FULL)
+            for (int k = lane; k < m; k += 32) coef[(size_t)k * ld + r] = 0.0;
+        return;
+    }
     const double eps = 2.220446049250313e-16;
-#define D_(i) d[(size_t)(i) * st]
-#define E_(i) e[(size_t)(i) * st]
-#define Z_(row, col) Z[((size_t)(row) * n + (col)) * st]
     for (int l = 0; l < n; ++l) {
         int iter = 0;
         for (;;) {
             int mm = l;
             for (; mm < n - 1; ++mm) {
-                const double dd = fabs(D_(mm)) + fabs(D_(mm + 1));
-                if (fabs(E_(mm)) <= eps * dd) break;
+                const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
+                if (fabs(e[mm]) <= eps * dd) break;
             }
             if (mm == l) break;
-            if (++iter > 60) return false;
-            double g = (D_(l + 1) - D_(l)) / (2.0 * E_(l));
-            double r = hypot(g, 1.0);
-            g = D_(mm) - D_(l) + E_(l) / (g + copysign(r, g));
-            double s = 1.0, c = 1.0, p = 0.0;
-            bool underflow = false;
-            for (int i = mm - 1; i >= l; --i) {
-                const double f = s * E_(i);
-                const double b = c * E_(i);
-                r = hypot(f, g);
-                E_(i + 1) = r;
-                if (r == 0.0) {
-                    D_(i + 1) -= p;
-                    E_(mm) = 0.0;
-                    underflow = true;
-                    break;
+            if (++iter > 60) {
+                if (lane == 0) s_bad = 1;
+                break;
+            }
+            __syncwarp();   // every lane has read d, e before lane 0 rewrites them
+            if (lane == 0) {
+                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+                double rr = sqrt(g * g + 1.0);
+                g = d[mm] - d[l] + e[l] / (g + copysign(rr, g));
+                double s = 1.0, c = 1.0, p = 0.0;
+                int nrot = 0;
+                bool split = false;
+                for (int i = mm - 1; i >= l; --i) {
+                    const double f = s * e[i];
+                    const double bb = c * e[i];
+                    rr = sqrt(f * f + g * g);
+                    e[i + 1] = rr;
+                    if (rr == 0.0) {
+                        d[i + 1] -= p;
+                        e[mm] = 0.0;
+                        split = true;
+                        break;
+                    }
+                    s = f / rr;
+                    c = g / rr;
+                    g = d[i + 1] - p;
+                    rr = (d[i] - g) * s + 2.0 * c * bb;
+                    p = s * rr;
+                    d[i + 1] = g + p;
+                    g = c * rr - bb;
+                    cs[i] = c;
+                    sn[i] = s;
+                    ++nrot;
                 }
-                s = f / r;
-                c = g / r;
-                g = D_(i + 1) - p;
-                r = (D_(i) - g) * s + 2.0 * c * b;
-                p = s * r;
-                D_(i + 1) = g + p;
-                g = c * r - b;
-                for (int row = 0; row < nz; ++row) {
-                    const double zf = Z_(row, i + 1);
-                    Z_(row, i + 1) = s * Z_(row, i) + c * zf;
-                    Z_(row, i) = c * Z_(row, i) - s * zf;
+                if (!split) {
+                    d[l] -= p;
+                    e[l] = g;
+                    e[mm] = 0.0;
+                }
+                s_nrot = nrot;
+            }
+            __syncwarp();
+            const int nrot = s_nrot;
+            for (int row = lane; row < nz; row += 32) {
+                double *zr = Z + row * zs;
+                for (int t = 0; t < nrot; ++t) {
+                    const int i = mm - 1 - t;
+                    const double zf = zr[i + 1];
+                    zr[i + 1] = sn[i] * zr[i] + cs[i] * zf;
+                    zr[i] = cs[i] * zr[i] - sn[i] * zf;
                 }
             }
-            if (underflow) continue;
-            D_(l) -= p;
-            E_(l) = g;
-            E_(mm) = 0.0;
+            __syncwarp();
         }
+        __syncwarp();
+        if (s_bad) break;
     }
-#undef D_
-#undef E_
-#undef Z_
-    return true;
-}
-
-// One thread per probe: q_l = sum_k U_1k^2 sqrt(theta_k).  status bit 1: a
-// Ritz value <= 0; bit 2: no convergence; bit 4: non-finite input.
-__global__ void k_quadrature(const double *__restrict__ a, const double *__restrict__ b,
-                             const int *__restrict__ length, int R, int ld, int m, double *__restrict__ q,
-                             int *__restrict__ status, double *__restrict__ work) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    const int n = length ? length[r] : m;
-    const size_t st = (size_t)R;
-    double *d = work + r, *e = work + (size_t)m * R + r, *z = work + (size_t)2 * m * R + r;
-    bool finite = true;
-    for (int k = 0; k < n; ++k) {
-        d[k * st] = a[(size_t)k * ld + r];
-        e[k * st] = (k < n - 1) ? b[(size_t)k * ld + r] : 0.0;
-        z[k * st] = (k == 0) ? 1.0 : 0.0;
-        finite = finite && isfinite(d[k * st]) && isfinite(e[k * st]);
+    __syncwarp();
+    // q = sum_k U_1k^2 sqrt(theta_k)
+    double part = 0.0;
+    bool pos = true;
+    for (int k = lane; k < n; k += 32) {
+        const double th = d[k];
+        if (th > 0.0)
+            part += Z[k] * Z[k] * sqrt(th);
+        else
+            pos = false;
     }
-    if (!finite) {
-        atomicOr(status, 4);
-        q[r] = 0.0;
-        return;
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    pos = __all_sync(0xffffffffu, pos);
+    if (lane == 0) {
+        q[r] = part;
+        if (!pos) atomicOr(status, 1);
+        if (s_bad) atomicOr(status, 2);
     }
-    if (!ql_implicit(d, e, z, n, 1, st)) atomicOr(status, 2);
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) {
-        const double th = d[k * st];
-        if (!(th > 0.0)) {
-            atomicOr(status, 1);
-            continue;
-        }
-        s += z[k * st] * z[k * st] * sqrt(th);
-    }
-    q[r] = s;
-}
-
-// Coefficients c = Delta^{-1/2} e_1 = U diag(theta^{-1/2}) U^T e_1 per probe
-// (w = C^{-1/2} v ~ sum_k c_k y_k), full eigenvectors in scratch.
-__global__ void k_inv_sqrt_coeffs(const double *__restrict__ a, const double *__restrict__ b,
-                                  const int *__restrict__ length, int R, int ld, int m, double *__restrict__ coef,
-                                  int *__restrict__ status, double *__restrict__ work) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    const int n = length[r];
-    const size_t st = (size_t)R;
-    double *d = work + r, *e = work + (size_t)m * R + r, *Z = work + (size_t)2 * m * R + r;
-    for (int k = 0; k < n; ++k) {
-        d[k * st] = a[(size_t)k * ld + r];
-        e[k * st] = (k < n - 1) ? b[(size_t)k * ld + r] : 0.0;
-        for (int j = 0; j < n; ++j) Z[((size_t)k * n + j) * st] = (k == j) ? 1.0 : 0.0;
-    }
-    if (!ql_implicit(d, e, Z, n, n, st)) atomicOr(status, 2);
-    for (int k = 0; k < m; ++k) {
-        double s = 0.0;
-        if (k < n) {
-            for (int j = 0; j < n; ++j) {
-                const double th = d[j * st];
-                if (!(th > 0.0)) {
-                    atomicOr(status, 1);
-                    continue;
+    if (FULL) {
+        // c_k = sum_j U_kj theta_j^{-1/2} U_1j
+        for (int k = lane; k < m; k += 32) {
+            double c = 0.0;
+            if (k < n)
+                for (int j = 0; j < n; ++j) {
+                    const double th = d[j];
+                    if (th > 0.0) c += Z[k * zs + j] * Z[j] / sqrt(th);
                 }
-                s += Z[((size_t)k * n + j) * st] * Z[(size_t)j * st] / sqrt(th);
-            }
+            coef[(size_t)k * ld + r] = c;
         }
-        coef[(size_t)k * ld + r] = s;
     }
 }
 
@@ -369,16 +382,17 @@ mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int 
     return MBD_OK;
 }
 
-mbd_status launch_quadrature_t(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
-                               int *status, double *work, cudaStream_t st) {
-    k_quadrature<<<(R + 63) / 64, 64, 0, st>>>(a, b, length, R, ld, m, q, status, work);
-    MBD_LAUNCH_CHECK();
-    return MBD_OK;
-}
-
-mbd_status launch_inv_sqrt_t(const double *a, const double *b, const int *length, int R, int ld, int m, double *coef,
-                             int *status, double *work, cudaStream_t st) {
-    k_inv_sqrt_coeffs<<<(R + 63) / 64, 64, 0, st>>>(a, b, length, R, ld, m, coef, status, work);
+mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
+                          double *coef, int *status, cudaStream_t st) {
+    const bool full = coef != nullptr;
+    const size_t smem = sizeof(double) * (size_t)(4 * m + (full ? m * (m + 1) : m));
+    if (full) {
+        if (smem > 48 * 1024)
+            MBD_CUDA_TRY(cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_tridiag<true><<<R, 32, smem, st>>>(a, b, length, R, ld, m, q, coef, status);
+    } else {
+        k_tridiag<false><<<R, 32, smem, st>>>(a, b, length, R, ld, m, q, nullptr, status);
+    }
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }

@@ -5,53 +5,39 @@
 // a_k = y_k^T l_k (Eqs. lk3, recurs2).
 #include "mbd_internal.cuh"
 
+#include <algorithm>
+
 namespace mbd {
 
 namespace {
 
-constexpr int kWarps = 8;          // warps per block in spread / field
-constexpr int kMaxPts = 16;        // mesh points per warp in one brick (brick <= 5x5x5)
+constexpr int kWarps = 8;          // warps per block in the field kernel
 
-template <class T> struct SpreadArgs {
-    const T *d;          // [N][3][ld] Cartesian dipoles
-    T *mesh;             // [K^3][ld]
-    int R, ld;
-    Geom g;
-    SplineView<T> sp;
-    BinView bins;
-};
+// ---------------------------------------------------------------- spreading
+// The dipole array D(k) = sum_j d_j . grad W_j(k) (Eq. dipolarr) is a sparse
+// matrix W^T (one row per mesh point, one nonzero per atom whose stencil covers
+// the point) times the dense block of dipoles [3N][probes].  W^T is built once
+// per geometry in a fixed atom order, so every mesh value is a sum in a fixed
+// order: spreading is deterministic and writes each mesh point once.
 
-// Deterministic spreading: one block owns one brick of mesh points and a chunk
-// of 32 probes (lane = probe); it visits every atom whose stencil can reach the
-// brick, in a fixed order, and writes each mesh point exactly once.  The
-// Cartesian dipole is first mapped to scaled-fractional components
-// e_beta = sum_alpha C_{beta alpha} d_alpha, so that
-//   D(k) += e_1 M'(t1) M(t2) M(t3) + e_2 M(t1) M'(t2) M(t3) + e_3 M(t1) M(t2) M'(t3).
-template <class T>
-__global__ void __launch_bounds__(kWarps * 32) k_spread(SpreadArgs<T> a) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = blockIdx.y * 32 + lane;
-    const bool valid = r < a.R;
-    const BinView &B = a.bins;
-    const int bidx = blockIdx.x;
-    const int bb3 = bidx % B.nb3, bb2 = (bidx / B.nb3) % B.nb2, bb1 = bidx / (B.nb3 * B.nb2);
-    const int o1 = bb1 * B.bs1, o2 = bb2 * B.bs2, o3 = bb3 * B.bs3;
-    const int P = B.bs1 * B.bs2 * B.bs3;
-    const int p = a.g.p;
-    int g1[kMaxPts], g2[kMaxPts], g3[kMaxPts];
-    T acc[kMaxPts];
-#pragma unroll
-    for (int q = 0; q < kMaxPts; ++q) {
-        const int pt = warp + kWarps * q;
-        acc[q] = T(0);
-        const int l3 = pt % B.bs3, l2 = (pt / B.bs3) % B.bs2, l1 = pt / (B.bs3 * B.bs2);
-        g1[q] = o1 + l1;
-        g2[q] = o2 + l2;
-        g3[q] = o3 + l3;
-    }
-    const T c00 = T(a.g.cmat[0]), c01 = T(a.g.cmat[1]), c02 = T(a.g.cmat[2]);
-    const T c10 = T(a.g.cmat[3]), c11 = T(a.g.cmat[4]), c12 = T(a.g.cmat[5]);
-    const T c20 = T(a.g.cmat[6]), c21 = T(a.g.cmat[7]), c22 = T(a.g.cmat[8]);
+// Rows of W^T: a thread per mesh point visits the atoms of the bricks whose
+// stencils can reach it (binned by their last stencil point) in a fixed order;
+// FILL = false counts, FILL = true writes the Cartesian weights
+//   dW/dR_alpha = sum_beta C_{beta alpha} dW/du_beta,
+//   dW/du = (M'(u1) M(u2) M(u3), M(u1) M'(u2) M(u3), M(u1) M(u2) M'(u3)),
+// from FP64 stencil weights.
+template <class T, bool FILL>
+__global__ void k_spread_rows(Geom g, BinView B, const int *__restrict__ top, const double *__restrict__ w64,
+                              const double *__restrict__ dw64, int *__restrict__ cnt_or_row,
+                              SpreadRec<T> *__restrict__ rec) {
+    const size_t npts = (size_t)g.K1 * g.K2 * g.K3;
+    const size_t pt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pt >= npts) return;
+    const int g3 = (int)(pt % g.K3), g2 = (int)((pt / g.K3) % g.K2), g1 = (int)(pt / ((size_t)g.K2 * g.K3));
+    const int bb1 = g1 / B.bs1, bb2 = g2 / B.bs2, bb3 = g3 / B.bs3;
+    const int p = g.p;
+    int c = 0;
+    const int base = FILL ? cnt_or_row[pt] : 0;
     for (int c1 = 0; c1 < B.nc1; ++c1) {
         const int t1 = (bb1 + c1) % B.nb1;
         for (int c2 = 0; c2 < B.nc2; ++c2) {
@@ -59,47 +45,97 @@ __global__ void __launch_bounds__(kWarps * 32) k_spread(SpreadArgs<T> a) {
             for (int c3 = 0; c3 < B.nc3; ++c3) {
                 const int t3 = (bb3 + c3) % B.nb3;
                 const int bin = (t1 * B.nb2 + t2) * B.nb3 + t3;
-                const int s0 = B.start[bin], s1 = B.start[bin + 1];
-                for (int s = s0; s < s1; ++s) {
+                for (int s = B.start[bin]; s < B.start[bin + 1]; ++s) {
                     const int j = B.atoms[s];
-                    T d0 = T(0), d1 = T(0), d2 = T(0);
-                    if (valid) {
-                        d0 = a.d[(size_t)(3 * j) * a.ld + r];
-                        d1 = a.d[(size_t)(3 * j + 1) * a.ld + r];
-                        d2 = a.d[(size_t)(3 * j + 2) * a.ld + r];
+                    int u1 = top[3 * j] - g1;
+                    if (u1 < 0) u1 += g.K1;
+                    int u2 = top[3 * j + 1] - g2;
+                    if (u2 < 0) u2 += g.K2;
+                    int u3 = top[3 * j + 2] - g3;
+                    if (u3 < 0) u3 += g.K3;
+                    if (u1 >= p || u2 >= p || u3 >= p) continue;
+                    if (FILL) {
+                        const double *w = w64 + (size_t)3 * p * j, *dw = dw64 + (size_t)3 * p * j;
+                        const double m1 = w[u1], m2 = w[p + u2], m3 = w[2 * p + u3];
+                        const double n1 = dw[u1], n2 = dw[p + u2], n3 = dw[2 * p + u3];
+                        const double gu0 = n1 * m2 * m3, gu1 = m1 * n2 * m3, gu2 = m1 * m2 * n3;
+                        SpreadRec<T> r;
+                        r.w0 = T(g.cmat[0] * gu0 + g.cmat[3] * gu1 + g.cmat[6] * gu2);
+                        r.w1 = T(g.cmat[1] * gu0 + g.cmat[4] * gu1 + g.cmat[7] * gu2);
+                        r.w2 = T(g.cmat[2] * gu0 + g.cmat[5] * gu1 + g.cmat[8] * gu2);
+                        r.atom = j;
+                        rec[base + c] = r;
                     }
-                    const T e0 = c00 * d0 + c01 * d1 + c02 * d2;
-                    const T e1 = c10 * d0 + c11 * d1 + c12 * d2;
-                    const T e2 = c20 * d0 + c21 * d1 + c22 * d2;
-                    const int top1 = a.sp.top[3 * j], top2 = a.sp.top[3 * j + 1], top3 = a.sp.top[3 * j + 2];
-                    const T *w = a.sp.w + (size_t)3 * p * j;
-                    const T *dw = a.sp.dw + (size_t)3 * p * j;
-#pragma unroll
-                    for (int q = 0; q < kMaxPts; ++q) {
-                        if (warp + kWarps * q >= P) break;
-                        int u1 = top1 - g1[q];
-                        if (u1 < 0) u1 += a.g.K1;
-                        if (u1 >= p) continue;
-                        int u2 = top2 - g2[q];
-                        if (u2 < 0) u2 += a.g.K2;
-                        if (u2 >= p) continue;
-                        int u3 = top3 - g3[q];
-                        if (u3 < 0) u3 += a.g.K3;
-                        if (u3 >= p) continue;
-                        const T m1 = w[u1], m2 = w[p + u2], m3 = w[2 * p + u3];
-                        const T n1 = dw[u1], n2 = dw[p + u2], n3 = dw[2 * p + u3];
-                        acc[q] += e0 * (n1 * m2 * m3) + e1 * (m1 * n2 * m3) + e2 * (m1 * m2 * n3);
-                    }
+                    ++c;
                 }
             }
         }
     }
-    if (!valid) return;
-#pragma unroll
-    for (int q = 0; q < kMaxPts; ++q) {
-        if (warp + kWarps * q >= P) break;
-        const size_t pt = ((size_t)g1[q] * a.g.K2 + g2[q]) * a.g.K3 + g3[q];
-        a.mesh[pt * a.ld + r] = acc[q];
+    if (!FILL) cnt_or_row[pt] = c;
+}
+
+// Exclusive scan of n counts (blocks of 4096), the block sums, and the fix-up.
+__global__ void __launch_bounds__(1024) k_scan_block(const int *__restrict__ in, int *__restrict__ out,
+                                                     int *__restrict__ bsum, int n) {
+    __shared__ int sh[1024];
+    const int tid = threadIdx.x;
+    const long long base = (long long)blockIdx.x * 4096 + tid * 4;
+    int v[4], tsum = 0;
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        tsum += v[k];
+    }
+    sh[tid] = tsum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int t = tid >= off ? sh[tid - off] : 0;
+        __syncthreads();
+        sh[tid] += t;
+        __syncthreads();
+    }
+    int excl = sh[tid] - tsum;
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = excl;
+        excl += v[k];
+    }
+    if (tid == 1023) bsum[blockIdx.x] = sh[1023];
+}
+__global__ void k_scan_sums(int *__restrict__ bsum, int nb, int *__restrict__ total) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long acc = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int t = bsum[b];
+        bsum[b] = (int)acc;
+        acc += t;
+    }
+    *total = acc > 0x7fffffffLL ? -1 : (int)acc;
+}
+__global__ void k_scan_add(int *__restrict__ out, const int *__restrict__ bsum, int n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += bsum[i / 4096];
+}
+
+// D = W^T d: a warp per mesh point, lane = probe (chunk of 32 per blockIdx.y).
+// Columns R..ld-1 (padding of an odd probe count) are written as zeros.
+template <class T>
+__global__ void __launch_bounds__(256) k_spread_csr(const T *__restrict__ d, T *__restrict__ mesh, int R, int ld,
+                                                    size_t npts, const int *__restrict__ row,
+                                                    const SpreadRec<T> *__restrict__ rec) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.y * 32 + lane;
+    const bool in_ld = r < ld;
+    const bool valid = r < R;
+    for (size_t pt = (size_t)blockIdx.x * 8 + warp; pt < npts; pt += (size_t)gridDim.x * 8) {
+        const int q0 = row[pt], q1 = row[pt + 1];
+        T acc = T(0);
+        for (int q = q0; q < q1; ++q) {
+            const SpreadRec<T> w = rec[q];
+            if (valid) {
+                const size_t o = (size_t)(3 * w.atom) * ld + r;
+                acc += w.w0 * d[o] + w.w1 * d[o + ld] + w.w2 * d[o + 2 * (size_t)ld];
+            }
+        }
+        if (in_ld) mesh[pt * ld + r] = acc;
     }
 }
 
@@ -185,42 +221,60 @@ template <class T> struct FFTArgs {
     int inner;           // complex elements per row (contiguous)
     int W;               // tile width (complex columns)
     int nst;
-    int radix[kMaxRadixStages];
+    unsigned long long radices;   // stage s radix = (radices >> 4 s) & 15
     int V;               // complex probe pairs per mesh point (fused pass: G index = e / V)
     int sign;            // -1 forward, +1 inverse (unfused passes)
 };
 
+template <class T, class C, int R> __device__ __forceinline__ void dft(C *v, int sign) {
+    if constexpr (R == 2) dft2<T>(v);
+    else if constexpr (R == 3) dft3<T>(v, sign);
+    else if constexpr (R == 4) dft4<T>(v, sign);
+    else if constexpr (R == 5) dft5<T>(v, sign);
+    else dft8<T>(v, sign);
+}
+
+// One radix-R Stockham stage over the K rows of a K x W tile in shared memory
+// (R compile-time, so the butterfly stays in registers).
+template <class T, class C, int R>
+__device__ __forceinline__ void stockham_stage(const C *__restrict__ in, C *__restrict__ out,
+                                               const C *__restrict__ tw, int K, int W, int Ns, int sign) {
+    const int nb = K / R;
+    const int step = K / (Ns * R);
+    for (int idx = threadIdx.x; idx < nb * W; idx += blockDim.x) {
+        const int j = idx / W, col = idx - j * W;
+        C v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = in[(j + q * nb) * W + col];
+        const int jm = j % Ns;
+        if (jm != 0) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C t = tw[q * jm * step];
+                if (sign > 0) t.y = -t.y;
+                v[q] = cmul(v[q], t);
+            }
+        }
+        dft<T, C, R>(v, sign);
+        const int base = (j / Ns) * Ns * R + jm;
+#pragma unroll
+        for (int q = 0; q < R; ++q) out[(base + q * Ns) * W + col] = v[q];
+    }
+}
+
 // Mixed-radix Stockham passes over the K rows of a K x W tile held in shared
 // memory; returns the buffer that holds the result (natural order).
 template <class T, class C>
-__device__ C *stockham(C *in, C *out, const FFTArgs<T> &a, int sign) {
-    const int K = a.K, W = a.W;
+__device__ C *stockham(C *in, C *out, const FFTArgs<T> &a, const C *tw, int sign) {
     int Ns = 1;
     for (int s = 0; s < a.nst; ++s) {
-        const int R = a.radix[s];
-        const int nb = K / R;
-        const int step = K / (Ns * R);
-        for (int idx = threadIdx.x; idx < nb * W; idx += blockDim.x) {
-            const int j = idx / W, col = idx - j * W;
-            C v[8];
-            for (int q = 0; q < R; ++q) v[q] = in[(j + q * nb) * W + col];
-            const int jm = j % Ns;
-            if (jm != 0) {
-                for (int q = 1; q < R; ++q) {
-                    C t = a.tw[q * jm * step];
-                    if (sign > 0) t.y = -t.y;
-                    v[q] = cmul(v[q], t);
-                }
-            }
-            switch (R) {
-                case 2: dft2<T>(v); break;
-                case 3: dft3<T>(v, sign); break;
-                case 4: dft4<T>(v, sign); break;
-                case 5: dft5<T>(v, sign); break;
-                default: dft8<T>(v, sign); break;
-            }
-            const int base = (j / Ns) * Ns * R + jm;
-            for (int q = 0; q < R; ++q) out[(base + q * Ns) * W + col] = v[q];
+        const int R = (int)((a.radices >> (4 * s)) & 15ull);
+        switch (R) {
+            case 2: stockham_stage<T, C, 2>(in, out, tw, a.K, a.W, Ns, sign); break;
+            case 3: stockham_stage<T, C, 3>(in, out, tw, a.K, a.W, Ns, sign); break;
+            case 4: stockham_stage<T, C, 4>(in, out, tw, a.K, a.W, Ns, sign); break;
+            case 5: stockham_stage<T, C, 5>(in, out, tw, a.K, a.W, Ns, sign); break;
+            default: stockham_stage<T, C, 8>(in, out, tw, a.K, a.W, Ns, sign); break;
         }
         __syncthreads();
         C *t = in;
@@ -239,6 +293,8 @@ __global__ void __launch_bounds__(256) k_fft_pass(FFTArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *b0 = reinterpret_cast<C *>(smem_raw);
     C *b1 = b0 + a.K * a.W;
+    C *tw = b1 + a.K * a.W;
+    for (int i = threadIdx.x; i < a.K; i += blockDim.x) tw[i] = a.tw[i];
     const int ncb = (a.inner + a.W - 1) / a.W;
     const size_t outer = blockIdx.x / ncb;
     const int c0 = (int)(blockIdx.x % ncb) * a.W;
@@ -251,7 +307,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FFTArgs<T> a) {
     __syncthreads();
     C *res;
     if (FUSED) {
-        res = stockham<T, C>(b0, b1, a, -1);
+        res = stockham<T, C>(b0, b1, a, tw, -1);
         C *other = (res == b0) ? b1 : b0;
         // G index: k1 = row, (k2, k3) = (c0 + col) / V
         for (int idx = threadIdx.x; idx < a.K * a.W; idx += blockDim.x) {
@@ -263,9 +319,9 @@ __global__ void __launch_bounds__(256) k_fft_pass(FFTArgs<T> a) {
             }
         }
         __syncthreads();
-        res = stockham<T, C>(res, other, a, +1);
+        res = stockham<T, C>(res, other, a, tw, +1);
     } else {
-        res = stockham<T, C>(b0, b1, a, a.sign);
+        res = stockham<T, C>(b0, b1, a, tw, a.sign);
     }
     for (int idx = threadIdx.x; idx < a.K * a.W; idx += blockDim.x) {
         const int row = idx / a.W, col = idx - row * a.W;
@@ -288,24 +344,97 @@ template <class T> struct FieldArgs {
     FieldOut<T> o;
 };
 
-// One warp per atom, lane = probe.  E* = E^rec + E^dir + E^self, then the
-// epilogue selected by o.mode.
-template <class T>
+// Vector loads/stores of VEC consecutive values (VEC in {1, 2, 4}).
+template <class T, int VEC> struct VecT;
+template <> struct VecT<float, 1> { using type = float; };
+template <> struct VecT<float, 2> { using type = float2; };
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<double, 1> { using type = double; };
+template <> struct VecT<double, 2> { using type = double2; };
+
+template <class T, int VEC> __device__ __forceinline__ void vload(const T *p, T *v) {
+    if constexpr (VEC == 4 && sizeof(T) == 8) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+        return;
+    } else {
+    using V = typename VecT<T, VEC>::type;
+    const V x = *reinterpret_cast<const V *>(p);
+    if constexpr (VEC == 1) {
+        v[0] = x;
+    } else if constexpr (VEC == 2) {
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    }
+    }
+}
+template <class T, int VEC> __device__ __forceinline__ void vstore(T *p, const T *v) {
+    if constexpr (VEC == 4 && sizeof(T) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+        return;
+    } else {
+    using V = typename VecT<T, VEC>::type;
+    V x;
+    if constexpr (VEC == 1) {
+        x = v[0];
+    } else if constexpr (VEC == 2) {
+        x.x = v[0];
+        x.y = v[1];
+    } else {
+        x.x = v[0];
+        x.y = v[1];
+        x.z = v[2];
+        x.w = v[3];
+    }
+    *reinterpret_cast<V *>(p) = x;
+    }
+}
+
+// One warp per atom; lane owns VEC consecutive probes.  E* = E^rec + E^dir +
+// E^self, then the epilogue selected by o.mode.  P = spline order (0: runtime).
+template <class T, int VEC, int PC>
 __global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = blockIdx.y * 32 + lane;
-    const bool valid = r < a.R;
+    const int r0 = (blockIdx.y * 32 + lane) * VEC;
+    const bool inld = r0 < a.ld;
     const int idx = blockIdx.x * kWarps + warp;
-    const int p = a.g.p;
-    double part = 0.0;
-    if (idx < a.g.N) {
+    const int p = PC > 0 ? PC : a.g.p;
+    double part[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) part[v] = 0.0;
+    if (idx < a.g.N && inld) {
         const int i = a.order[idx];
-        T E0 = T(0), E1 = T(0), E2 = T(0);
+        T E0[VEC], E1[VEC], E2[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) E0[v] = E1[v] = E2[v] = T(0);
         if (a.o.terms & MBD_TERM_RECIP) {
-            T f0 = T(0), f1 = T(0), f2 = T(0);
+            T f0[VEC], f1[VEC], f2[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) f0[v] = f1[v] = f2[v] = T(0);
             const int top1 = a.sp.top[3 * i], top2 = a.sp.top[3 * i + 1], top3 = a.sp.top[3 * i + 2];
             const T *w = a.sp.w + (size_t)3 * p * i;
             const T *dw = a.sp.dw + (size_t)3 * p * i;
+            T wc[PC > 0 ? PC : kMaxOrder], dc[PC > 0 ? PC : kMaxOrder];
+            int k3s[PC > 0 ? PC : kMaxOrder];
+#pragma unroll
+            for (int t3 = 0; t3 < (PC > 0 ? PC : kMaxOrder); ++t3) {
+                if (t3 < p) {
+                    wc[t3] = w[2 * p + t3];
+                    dc[t3] = dw[2 * p + t3];
+                    int k3 = top3 - t3;
+                    if (k3 < 0) k3 += a.g.K3;
+                    k3s[t3] = k3;
+                }
+            }
             for (int t1 = 0; t1 < p; ++t1) {
                 int k1 = top1 - t1;
                 if (k1 < 0) k1 += a.g.K1;
@@ -315,22 +444,33 @@ __global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a) {
                     if (k2 < 0) k2 += a.g.K2;
                     const T wb = w[p + t2], db = dw[p + t2];
                     const T ab = wa * wb, Ab = da * wb, aB = wa * db;
-                    const size_t rowbase = ((size_t)k1 * a.g.K2 + k2) * a.g.K3;
-                    for (int t3 = 0; t3 < p; ++t3) {
-                        int k3 = top3 - t3;
-                        if (k3 < 0) k3 += a.g.K3;
-                        const T wc = w[2 * p + t3], dc = dw[2 * p + t3];
-                        const T phi = valid ? a.mesh[(rowbase + k3) * a.ld + r] : T(0);
-                        f0 += (Ab * wc) * phi;
-                        f1 += (aB * wc) * phi;
-                        f2 += (ab * dc) * phi;
+                    const T *rowp = a.mesh + ((size_t)k1 * a.g.K2 + k2) * a.g.K3 * a.ld + r0;
+#pragma unroll
+                    for (int t3 = 0; t3 < (PC > 0 ? PC : kMaxOrder); ++t3) {
+                        if (t3 < p) {
+                            T phi[VEC];
+                            vload<T, VEC>(rowp + (size_t)k3s[t3] * a.ld, phi);
+                            const T c0 = Ab * wc[t3], c1 = aB * wc[t3], c2 = ab * dc[t3];
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                f0[v] += c0 * phi[v];
+                                f1[v] += c1 * phi[v];
+                                f2[v] += c2 * phi[v];
+                            }
+                        }
                     }
                 }
             }
             // E^rec_alpha = sum_beta C_{beta alpha} f_beta
-            E0 += T(a.g.cmat[0]) * f0 + T(a.g.cmat[3]) * f1 + T(a.g.cmat[6]) * f2;
-            E1 += T(a.g.cmat[1]) * f0 + T(a.g.cmat[4]) * f1 + T(a.g.cmat[7]) * f2;
-            E2 += T(a.g.cmat[2]) * f0 + T(a.g.cmat[5]) * f1 + T(a.g.cmat[8]) * f2;
+            const T m00 = T(a.g.cmat[0]), m01 = T(a.g.cmat[1]), m02 = T(a.g.cmat[2]);
+            const T m10 = T(a.g.cmat[3]), m11 = T(a.g.cmat[4]), m12 = T(a.g.cmat[5]);
+            const T m20 = T(a.g.cmat[6]), m21 = T(a.g.cmat[7]), m22 = T(a.g.cmat[8]);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                E0[v] += m00 * f0[v] + m10 * f1[v] + m20 * f2[v];
+                E1[v] += m01 * f0[v] + m11 * f1[v] + m21 * f2[v];
+                E2[v] += m02 * f0[v] + m12 * f1[v] + m22 * f2[v];
+            }
         }
         if (a.o.terms & MBD_TERM_REAL) {
             const int nb0 = a.pr.row[i], nb1 = a.pr.row[i + 1];
@@ -338,72 +478,103 @@ __global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a) {
                 const int j = a.pr.col[nb];
                 const T *A = a.pr.A + 6 * (size_t)nb;
                 const T A0 = A[0], A1 = A[1], A2 = A[2], A3 = A[3], A4 = A[4], A5 = A[5];
-                T x = T(0), y = T(0), z = T(0);
-                if (valid) {
-                    x = a.d[(size_t)(3 * j) * a.ld + r];
-                    y = a.d[(size_t)(3 * j + 1) * a.ld + r];
-                    z = a.d[(size_t)(3 * j + 2) * a.ld + r];
+                T x[VEC], y[VEC], z[VEC];
+                const T *dj = a.d + (size_t)(3 * j) * a.ld + r0;
+                vload<T, VEC>(dj, x);
+                vload<T, VEC>(dj + a.ld, y);
+                vload<T, VEC>(dj + 2 * (size_t)a.ld, z);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    E0[v] += A0 * x[v] + A1 * y[v] + A2 * z[v];
+                    E1[v] += A1 * x[v] + A3 * y[v] + A4 * z[v];
+                    E2[v] += A2 * x[v] + A4 * y[v] + A5 * z[v];
                 }
-                E0 += A0 * x + A1 * y + A2 * z;
-                E1 += A1 * x + A3 * y + A4 * z;
-                E2 += A2 * x + A4 * y + A5 * z;
             }
         }
-        if ((a.o.terms & MBD_TERM_SELF) && valid) {
+        if (a.o.terms & MBD_TERM_SELF) {
             const T c = T(a.self_coef);
-            E0 += c * a.d[(size_t)(3 * i) * a.ld + r];
-            E1 += c * a.d[(size_t)(3 * i + 1) * a.ld + r];
-            E2 += c * a.d[(size_t)(3 * i + 2) * a.ld + r];
+            T x[VEC], y[VEC], z[VEC];
+            const T *di = a.d + (size_t)(3 * i) * a.ld + r0;
+            vload<T, VEC>(di, x);
+            vload<T, VEC>(di + a.ld, y);
+            vload<T, VEC>(di + 2 * (size_t)a.ld, z);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                E0[v] += c * x[v];
+                E1[v] += c * y[v];
+                E2[v] += c * z[v];
+            }
         }
-        if (valid) {
-            const double E[3] = {double(E0), double(E1), double(E2)};
-            const size_t rows[3] = {(size_t)(3 * i) * a.ld + r, (size_t)(3 * i + 1) * a.ld + r,
-                                    (size_t)(3 * i + 2) * a.ld + r};
-            if (a.o.mode == kFieldOut) {
-                for (int c = 0; c < 3; ++c) a.o.out[rows[c]] = E[c];
-            } else if (a.o.mode == kFieldApply) {
-                const double w2 = a.w2[i], gi = a.g_at[i];
-                for (int c = 0; c < 3; ++c) a.o.out[rows[c]] = w2 * a.o.xin[rows[c]] + gi * E[c];
-            } else {
-                const double invb = a.o.lz.invb[r];
-                const double w2 = a.w2[i], gi = a.g_at[i];
-                double *Yk = a.o.lz.Y + (size_t)a.o.k * (size_t)(3 * a.g.N) * a.ld;
-                for (int c = 0; c < 3; ++c) {
-                    const double y = Yk[rows[c]] * invb;
-                    const double l = w2 * y + gi * E[c] * invb;
-                    Yk[rows[c]] = y;
-                    a.o.lz.L[rows[c]] = l;
-                    part += y * l;
+        const size_t o0 = (size_t)(3 * i) * a.ld + r0;
+        const T *Ec[3] = {E0, E1, E2};
+        if (a.o.mode == kFieldOut) {
+            for (int c = 0; c < 3; ++c) {
+                double e[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) e[v] = double(Ec[c][v]);
+                vstore<double, VEC>(a.o.out + o0 + (size_t)c * a.ld, e);
+            }
+        } else if (a.o.mode == kFieldApply) {
+            const double w2 = a.w2[i], gi = a.g_at[i];
+            for (int c = 0; c < 3; ++c) {
+                double x[VEC], y[VEC];
+                vload<double, VEC>(a.o.xin + o0 + (size_t)c * a.ld, x);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) y[v] = w2 * x[v] + gi * double(Ec[c][v]);
+                vstore<double, VEC>(a.o.out + o0 + (size_t)c * a.ld, y);
+            }
+        } else {
+            double invb[VEC];
+            vload<double, VEC>(a.o.lz.invb + r0, invb);
+            const double w2 = a.w2[i], gi = a.g_at[i];
+            double *Yk = a.o.lz.Y + (size_t)a.o.k * (size_t)(3 * a.g.N) * a.ld;
+            for (int c = 0; c < 3; ++c) {
+                double ys[VEC], y[VEC], l[VEC];
+                vload<double, VEC>(Yk + o0 + (size_t)c * a.ld, ys);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    y[v] = ys[v] * invb[v];
+                    l[v] = w2 * y[v] + gi * double(Ec[c][v]) * invb[v];
+                    part[v] += y[v] * l[v];
                 }
+                vstore<double, VEC>(Yk + o0 + (size_t)c * a.ld, y);
+                vstore<double, VEC>(a.o.lz.L + o0 + (size_t)c * a.ld, l);
             }
         }
     }
     if (a.o.mode != kFieldLanczos) return;
     // a_k = y_k^T l_k: block partial per probe, then the last block sums the
     // partials in block order (deterministic) and resets the counter.
-    __shared__ double red[kWarps][32];
+    __shared__ double red[kWarps][32 * VEC];
     __shared__ bool last;
-    red[warp][lane] = part;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) red[warp][lane * VEC + v] = part[v];
     __syncthreads();
-    if (warp == 0) {
+    const int nloc = 32 * VEC;
+    const int rbase = blockIdx.y * nloc;
+    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
         double s = 0.0;
-        for (int w = 0; w < kWarps; ++w) s += red[w][lane];
-        if (valid) a.o.lz.partial[(size_t)blockIdx.x * a.ld + r] = s;
-        __threadfence();
+        for (int w = 0; w < kWarps; ++w) s += red[w][t];
+        if (rbase + t < a.R) a.o.lz.partial[(size_t)blockIdx.x * a.ld + rbase + t] = s;
     }
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(&a.o.lz.counter[blockIdx.y], 1u);
         last = (prev == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && warp == 0) {
+    if (last) {
         __threadfence();
-        double s = 0.0;
-        if (valid)
-            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&a.o.lz.partial[(size_t)b * a.ld + r]);
-        if (valid) a.o.lz.a[(size_t)a.o.k * a.ld + r] = s;
-        if (lane == 0) a.o.lz.counter[blockIdx.y] = 0u;
+        for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
+            const int r = rbase + t;
+            if (r < a.R) {
+                double s = 0.0;
+                for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&a.o.lz.partial[(size_t)b * a.ld + r]);
+                a.o.lz.a[(size_t)a.o.k * a.ld + r] = s;
+            }
+        }
+        if (threadIdx.x == 0) a.o.lz.counter[blockIdx.y] = 0u;
     }
 }
 
@@ -426,24 +597,50 @@ Geom geom_of(const mbd_system *s) {
 
 }  // namespace
 
+template <class T> mbd_status build_spread_matrix(mbd_system *s) {
+    PrecData<T> &P = prec<T>(s);
+    const Geom g = geom_of(s);
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    if (npts >= 0x7fffffffULL) return MBD_ERR_UNSUPPORTED;
+    MBD_TRY(P.srow.ensure(sizeof(int) * (npts + 1)));
+    DevBuf cnt, bsum, total;
+    const int n = (int)npts;
+    const int nb = (n + 4095) / 4096;
+    MBD_TRY(cnt.ensure(sizeof(int) * npts));
+    MBD_TRY(bsum.ensure(sizeof(int) * nb));
+    MBD_TRY(total.ensure(sizeof(int)));
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((npts + threads - 1) / threads);
+    k_spread_rows<T, false><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
+                                                              s->dw64_d.as<double>(), cnt.as<int>(), nullptr);
+    MBD_LAUNCH_CHECK();
+    k_scan_block<<<nb, 1024, 0, s->stream>>>(cnt.as<int>(), P.srow.template as<int>(), bsum.as<int>(), n);
+    MBD_LAUNCH_CHECK();
+    k_scan_sums<<<1, 32, 0, s->stream>>>(bsum.as<int>(), nb, P.srow.template as<int>() + n);
+    MBD_LAUNCH_CHECK();
+    k_scan_add<<<(n + 255) / 256, 256, 0, s->stream>>>(P.srow.template as<int>(), bsum.as<int>(), n);
+    MBD_LAUNCH_CHECK();
+    int nnz = 0;
+    MBD_CUDA_TRY(cudaMemcpyAsync(&nnz, P.srow.template as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (nnz < 0) return MBD_ERR_UNSUPPORTED;
+    MBD_TRY(P.srec.ensure(sizeof(SpreadRec<T>) * (size_t)(nnz > 0 ? nnz : 1)));
+    k_spread_rows<T, true><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
+                                                             s->dw64_d.as<double>(), P.srow.template as<int>(),
+                                                             P.srec.template as<SpreadRec<T>>());
+    MBD_LAUNCH_CHECK();
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));   // cnt, bsum, total are freed on return
+    return MBD_OK;
+}
+
 template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, int R, int ld) {
     PrecData<T> &P = prec<T>(s);
-    SpreadArgs<T> a;
-    a.d = d;
-    a.mesh = mesh;
-    a.R = R;
-    a.ld = ld;
-    a.g = geom_of(s);
-    a.sp = SplineView<T>{s->top_d.as<int>(), P.w.template as<T>(), P.dw.template as<T>(), P.d2w.template as<T>()};
-    a.bins = s->bins;
-    dim3 grid(s->bins.nb1 * s->bins.nb2 * s->bins.nb3, (R + 31) / 32);
-    k_spread<T><<<grid, kWarps * 32, 0, s->stream>>>(a);
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    const unsigned gx = (unsigned)std::min<size_t>((npts + 7) / 8, 152 * 64);
+    dim3 grid(gx, (ld + 31) / 32);
+    k_spread_csr<T><<<grid, 256, 0, s->stream>>>(d, mesh, R, ld, npts, P.srow.template as<int>(),
+                                                 P.srec.template as<SpreadRec<T>>());
     MBD_LAUNCH_CHECK();
-    // zero the padded probe columns so that the complex pairing never reads junk
-    if (R < ld) {
-        MBD_CUDA_TRY(cudaMemset2DAsync(mesh + R, sizeof(T) * ld, 0, sizeof(T) * (ld - R),
-                                       (size_t)s->K[0] * s->K[1] * s->K[2], s->stream));
-    }
     return MBD_OK;
 }
 
@@ -452,7 +649,7 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld) {
     PrecData<T> &P = prec<T>(s);
     const int V = ld / 2;
     const int K1 = s->K[0], K2 = s->K[1], K3 = s->K[2];
-    const int Wmax = sizeof(T) == 4 ? 16 : 8;
+    const int Wmax = sizeof(T) == 4 ? 32 : 16;
     auto run = [&](int dim, int outer, int inner, int sign, bool fused) -> mbd_status {
         FFTArgs<T> a;
         a.data = reinterpret_cast<C *>(mesh);
@@ -460,12 +657,13 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld) {
         a.G = P.G.template as<T>();
         a.K = s->fft[dim].K;
         a.nst = s->fft[dim].nst;
-        for (int k = 0; k < kMaxRadixStages; ++k) a.radix[k] = s->fft[dim].radix[k];
+        a.radices = 0ull;
+        for (int k = 0; k < a.nst; ++k) a.radices |= (unsigned long long)s->fft[dim].radix[k] << (4 * k);
         a.inner = inner;
         a.W = inner < Wmax ? inner : Wmax;
         a.V = V;
         a.sign = sign;
-        const size_t smem = 2 * sizeof(C) * (size_t)a.K * a.W;
+        const size_t smem = sizeof(C) * (2 * (size_t)a.K * a.W + a.K);
         dim3 grid((unsigned)((size_t)outer * ((inner + a.W - 1) / a.W)));
         if (fused) {
             if (smem > 48 * 1024)
@@ -505,14 +703,30 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     a.w2 = s->w2_d.as<double>();
     a.self_coef = -4.0 * s->ewald_beta * s->ewald_beta * s->ewald_beta / (3.0 * 1.77245385090551602730);
     a.o = o;
-    dim3 grid((s->N + kWarps - 1) / kWarps, (R + 31) / 32);
-    k_field<T><<<grid, kWarps * 32, 0, s->stream>>>(a);
+    const int vec = (sizeof(T) == 4 && ld % 4 == 0 && ld >= 128) ? 4 : ((ld % 2 == 0 && ld >= 64) ? 2 : 1);
+    dim3 grid((s->N + kWarps - 1) / kWarps, (ld + 32 * vec - 1) / (32 * vec));
+#define MBD_FIELD_LAUNCH(V, P) k_field<T, V, P><<<grid, kWarps * 32, 0, s->stream>>>(a)
+    if (vec == 4) {
+        if constexpr (sizeof(T) == 4) {
+            if (s->p == 6) MBD_FIELD_LAUNCH(4, 6);
+            else MBD_FIELD_LAUNCH(4, 0);
+        }
+    } else if (vec == 2) {
+        if (s->p == 6) MBD_FIELD_LAUNCH(2, 6);
+        else MBD_FIELD_LAUNCH(2, 0);
+    } else {
+        if (s->p == 6) MBD_FIELD_LAUNCH(1, 6);
+        else MBD_FIELD_LAUNCH(1, 0);
+    }
+#undef MBD_FIELD_LAUNCH
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }
 
 int field_blocks(int N) { return (N + kWarps - 1) / kWarps; }
 
+template mbd_status build_spread_matrix<double>(mbd_system *);
+template mbd_status build_spread_matrix<float>(mbd_system *);
 template mbd_status launch_spread<double>(mbd_system *, const double *, double *, int, int);
 template mbd_status launch_spread<float>(mbd_system *, const float *, float *, int, int);
 template mbd_status launch_convolve<double>(mbd_system *, double *, int);

@@ -12,6 +12,54 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kSqrtPi = 1.77245385090551602730;
 
+// dA_ab / dr_c for the real-space pair tensor (FP64):
+//   erfc part  -B2 (delta_ab r_c + delta_ac r_b + delta_bc r_a) + B3 r_a r_b r_c
+//   damping    -d/dr_c [(1 - s) T_ab] with T_ab = delta_ab/r^3 - 3 r_a r_b / r^5
+__device__ void pair_tensor_grad(double rx, double ry, double rz, double rsum, double beta, double r_cut,
+                                      double damp_cut, double damp_beta, double damp_d, double out[18]) {
+    const double rv[3] = {rx, ry, rz};
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const double rho = sqrt(r2);
+    // A = c_id I - c_rr r r^T with radial c_id, c_rr; dA_ab/dr_c =
+    //   (c_id'/rho) r_c delta_ab - (c_rr'/rho) r_c r_a r_b - c_rr (delta_ac r_b + delta_bc r_a)
+    double cid_p = 0.0, crr = 0.0, crr_p = 0.0;   // c_id'/rho, c_rr, c_rr'/rho
+    if (rho < r_cut) {
+        const double e = exp(-beta * beta * r2);
+        const double b0 = erfc(beta * rho) / rho;
+        const double b1 = (b0 + 2.0 * beta / kSqrtPi * e) / r2;
+        const double b2 = (3.0 * b1 + 4.0 * beta * beta * beta / kSqrtPi * e) / r2;
+        const double b3 = (5.0 * b2 + 8.0 * beta * beta * beta * beta * beta / kSqrtPi * e) / r2;
+        // (1/r) dB_n/dr = -B_{n+1}
+        cid_p += -b2;
+        crr += b2;
+        crr_p += -b3;
+    }
+    if (rho < damp_cut) {
+        const double x = damp_d * (rho / (damp_beta * rsum) - 1.0);
+        const double oms = 1.0 / (1.0 + exp(x));          // 1 - s
+        const double s = 1.0 - oms;
+        const double dsdr = damp_d / (damp_beta * rsum) * s * oms;
+        const double r3 = r2 * rho, r5 = r3 * r2;
+        // subtract (1-s) T:  c_id -= oms / r^3,  c_rr -= 3 oms / r^5
+        // d/dr (oms / r^3) = -dsdr / r^3 - 3 oms / r^4 ;  d/dr (3 oms / r^5) = -3 dsdr / r^5 - 15 oms / r^6
+        cid_p -= (-dsdr / r3 - 3.0 * oms / (r3 * rho)) / rho;
+        crr -= 3.0 * oms / r5;
+        crr_p -= (-3.0 * dsdr / r5 - 15.0 * oms / (r5 * rho)) / rho;
+    }
+    int o = 0;
+    for (int ab = 0; ab < 6; ++ab) {
+        const int ia = ab < 3 ? 0 : (ab < 5 ? 1 : 2);
+        const int ib = ab < 3 ? ab : (ab < 5 ? ab - 2 : 2);
+        for (int c = 0; c < 3; ++c) {
+            double v = -crr_p * rv[c] * rv[ia] * rv[ib];
+            if (ia == ib) v += cid_p * rv[c];
+            if (ia == c) v -= crr * rv[ib];
+            if (ib == c) v -= crr * rv[ia];
+            out[o++] = v;
+        }
+    }
+}
+
 // Real-space pair tensor of E^dir with the damping correction (Eq. fld_ewald):
 //   A(r) = [|r| < r_cut] (B1 I - B2 r r^T) - [|r| < damp_cut] (1 - s(|r|)) T(r)
 // with Smith's erfc-screened B1, B2 and the bare T(r) = (r^2 I - 3 r r^T)/r^5.
@@ -20,7 +68,8 @@ template <class T>
 __global__ void k_pair_tensors(int N, const double *__restrict__ pos, const double *__restrict__ rvdw,
                                const int *__restrict__ row, const int *__restrict__ col,
                                const int *__restrict__ shift, Geom g, double beta, double r_cut,
-                               double damp_cut, double damp_beta, double damp_d, T *__restrict__ A) {
+                               double damp_cut, double damp_beta, double damp_d, T *__restrict__ A,
+                               T *__restrict__ dA) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= N) return;
@@ -58,6 +107,10 @@ __global__ void k_pair_tensors(int N, const double *__restrict__ pos, const doub
         a[3] = T(c_id - c_rr * ry * ry);
         a[4] = T(-c_rr * ry * rz);
         a[5] = T(c_id - c_rr * rz * rz);
+        double g[18];
+        pair_tensor_grad(rx, ry, rz, rvdw[i] + rvdw[j], beta, r_cut, damp_cut, damp_beta, damp_d, g);
+        T *ga = dA + 18 * (size_t)nb;
+        for (int c = 0; c < 18; ++c) ga[c] = T(g[c]);
     }
 }
 
@@ -94,7 +147,8 @@ __device__ void bspline_stencil(double x, int p, double *m, double *dm, double *
 // stencil weights of mesh points top - t (mod K).
 template <class T>
 __global__ void k_splines(int N, const double *__restrict__ pos, Geom g, int *__restrict__ top,
-                          T *__restrict__ w, T *__restrict__ dw, T *__restrict__ d2w) {
+                          T *__restrict__ w, T *__restrict__ dw, T *__restrict__ d2w, double *__restrict__ w64,
+                          double *__restrict__ dw64) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 3 * N) return;
     const int i = idx / 3, a = idx % 3;
@@ -115,6 +169,8 @@ __global__ void k_splines(int N, const double *__restrict__ pos, Geom g, int *__
         w[(size_t)idx * g.p + t] = T(m[t]);
         dw[(size_t)idx * g.p + t] = T(dm[t]);
         d2w[(size_t)idx * g.p + t] = T(d2m[t]);
+        w64[(size_t)idx * g.p + t] = m[t];
+        dw64[(size_t)idx * g.p + t] = dm[t];
     }
 }
 
@@ -174,6 +230,7 @@ template <> PrecData<float> &prec<float>(mbd_system *s) { return s->f32; }
 template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st) {
     PrecData<T> &P = prec<T>(s);
     MBD_TRY(P.pairA.ensure(sizeof(T) * 6 * (size_t)(s->nnz > 0 ? s->nnz : 1)));
+    MBD_TRY(P.pairdA.ensure(sizeof(T) * 18 * (size_t)(s->nnz > 0 ? s->nnz : 1)));
     if (s->nnz == 0) return MBD_OK;
     const Geom g = make_geom(s);
     const int threads = 256;
@@ -181,7 +238,7 @@ template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st
     k_pair_tensors<T><<<blocks, threads, 0, st>>>(s->N, s->pos_d.as<double>(), s->rvdw_d.as<double>(),
                                                   s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(), g,
                                                   s->ewald_beta, s->r_cut, s->damp_cut, s->damp_beta, s->damp_d,
-                                                  P.pairA.template as<T>());
+                                                  P.pairA.template as<T>(), P.pairdA.template as<T>());
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }
@@ -192,10 +249,13 @@ template <class T> mbd_status launch_splines(mbd_system *s, cudaStream_t st) {
     MBD_TRY(P.w.ensure(sizeof(T) * n));
     MBD_TRY(P.dw.ensure(sizeof(T) * n));
     MBD_TRY(P.d2w.ensure(sizeof(T) * n));
+    MBD_TRY(s->w64_d.ensure(sizeof(double) * n));
+    MBD_TRY(s->dw64_d.ensure(sizeof(double) * n));
     const Geom g = make_geom(s);
     const int threads = 256;
     k_splines<T><<<(3 * s->N + threads - 1) / threads, threads, 0, st>>>(
-        s->N, s->pos_d.as<double>(), g, s->top_d.as<int>(), P.w.template as<T>(), P.dw.template as<T>(), P.d2w.template as<T>());
+        s->N, s->pos_d.as<double>(), g, s->top_d.as<int>(), P.w.template as<T>(), P.dw.template as<T>(),
+        P.d2w.template as<T>(), s->w64_d.as<double>(), s->dw64_d.as<double>());
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }

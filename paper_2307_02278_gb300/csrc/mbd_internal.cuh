@@ -109,8 +109,18 @@ struct LanczosView {
 // ---------------------------------------------------------------- per-system state
 struct SystemData;
 
+// One nonzero of the transposed stencil matrix: the Cartesian weights
+// dW_j(k)/dR_j of atom j at mesh point k (row = k).  For float the atom index
+// travels in the .w component (bit pattern), for double in a separate word.
+template <class T> struct SpreadRec;
+template <> struct __align__(16) SpreadRec<float> { float w0, w1, w2; int atom; };
+template <> struct __align__(16) SpreadRec<double> { double w0, w1, w2; int atom; int pad; };
+
 template <class T> struct PrecData {
     DevBuf pairA;       // [nnz][6]
+    DevBuf pairdA;      // [nnz][18] dA_ab/dr_c (forces)
+    DevBuf srow;        // [K^3 + 1] CSR row pointers of the spread matrix
+    DevBuf srec;        // [216 N] SpreadRec<T>
     DevBuf w, dw, d2w;  // [N][3][p]
     DevBuf G;           // [K1K2K3] influence function
     DevBuf tw1, tw2, tw3;   // twiddles [K] complex per dimension
@@ -156,6 +166,7 @@ struct mbd_system {
     mbd::DevBuf pos_d, g_d, w2_d, rvdw_d;            // [N][3], [N], [N], [N]
     mbd::DevBuf row_d, col_d, shift_d;              // CSR
     mbd::DevBuf top_d;                              // [N][3]
+    mbd::DevBuf w64_d, dw64_d;                      // [N][3][p] FP64 stencil weights (setup)
     mbd::DevBuf bin_start_d, bin_atoms_d, order_d;  // spread bins; field atom order
     mbd::BinView bins;
     long long nnz;
@@ -181,6 +192,7 @@ template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod
 
 // mesh stages
 template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, int R, int ld);
+template <class T> mbd_status build_spread_matrix(mbd_system *s);
 template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld);   // in place
 enum FieldMode { kFieldOut = 0, kFieldApply = 1, kFieldLanczos = 2 };
 template <class T> struct FieldOut {
@@ -197,10 +209,9 @@ template <class T> mbd_status launch_field(mbd_system *s, const T *d, const T *m
 // Lanczos
 mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int m, uint64_t seed, int R, int ld,
                              int rows, const double *g, void *dout, int dtype_bytes, int nblk);
-mbd_status launch_quadrature_t(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
-                               int *status, double *work, cudaStream_t st);
-mbd_status launch_inv_sqrt_t(const double *a, const double *b, const int *length, int R, int ld, int m, double *coef,
-                             int *status, double *work, cudaStream_t st);
+// q [R] and, when coef != nullptr, c = Delta^{-1/2} e_1 as coef [m][ld]
+mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
+                          double *coef, int *status, cudaStream_t st);
 mbd_status launch_energy_reduce(const double *q, int R, int dim, double omega_sum, double *scal, cudaStream_t st);
 mbd_status launch_probes(uint64_t seed, int first, int R, int dim, double *v, cudaStream_t st);
 mbd_status launch_dense_step(const double *c, int dim, const LanczosView &lz, int k, int R, int ld, int nblk,

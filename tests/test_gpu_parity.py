@@ -248,3 +248,25 @@ def test_water3000_sampled(mbd):
     np.testing.assert_allclose(det["q"][:3], q_ref, rtol=1e-8)
     em = mbd.MBDSystem.from_workload(s, precision="mixed").lanczos_energy(s.n_probes, s.n_steps, s.probe_seed)
     assert abs(em - e) <= 1e-5 * abs(e)
+
+
+# ------------------------------------------------------------------ kernel variants
+@pytest.mark.parametrize("p", [4, 8])
+@pytest.mark.parametrize("nvec", [3, 64, 128])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_apply_C_orders_and_widths(mbd, p, nvec, precision):
+    """Spline orders other than 6 and probe blocks of 1, 2 and 4 probes per lane."""
+    s = _small(mesh=(20, 16, 18)).with_(spline_order=p)
+    g = mbd.MBDSystem.from_workload(s, precision=precision)
+    x = np.random.default_rng(10 + p + nvec).normal(size=(nvec, 3 * s.n_atoms))
+    y = g.apply_C(_t(x)).cpu().numpy()
+    tol = 1e-11 if precision == "fp64" else 2e-6
+    assert _rel(y, Operator(s, "spme")(x)) < tol
+
+
+@pytest.mark.parametrize("R", [64, 128, 5])
+def test_lanczos_probe_widths(mbd, R):
+    s = _small()
+    e, det = mbd.MBDSystem.from_workload(s).lanczos_energy(R, 8, 1234, details=True)
+    q_ref, _, _, _ = slq(Operator(s, "spme"), 3 * s.n_atoms, R, 8, 1234)
+    np.testing.assert_allclose(det["q"], q_ref, rtol=1e-8)
