@@ -514,11 +514,17 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     MBD_TRY(s->b.ensure(sizeof(double) * (size_t)m * ld));
     MBD_TRY(s->invb.ensure(sizeof(double) * ld));
     MBD_TRY(s->length.ensure(sizeof(int) * ld));
-    MBD_TRY(s->partial.ensure(sizeof(double) * (size_t)std::max(z.nblk, field_nblk) * ld));
-    const size_t cbytes = sizeof(unsigned) * (size_t)std::max(nchunk, 64);
-    if (s->counter.bytes < cbytes) {
+    const int maxblk = std::max(z.nblk, field_nblk);
+    const int ngroups = (maxblk + kRedGroup - 1) / kRedGroup;
+    MBD_TRY(s->partial.ensure(sizeof(double) * (size_t)maxblk * ld));
+    MBD_TRY(s->gpartial.ensure(sizeof(double) * (size_t)ngroups * ld));
+    z.v.cstride = ngroups + 1;
+    // probe chunks of 32 (prologue) or 32 * VEC (field): 32 is the finest
+    const size_t cbytes = sizeof(unsigned) * (size_t)nchunk * z.v.cstride;
+    if (s->counter.bytes < cbytes || s->counter_stride != z.v.cstride) {
         MBD_TRY(s->counter.ensure(cbytes));
         MBD_CUDA_TRY(cudaMemsetAsync(s->counter.ptr, 0, s->counter.bytes, s->stream));
+        s->counter_stride = z.v.cstride;
     }
     MBD_TRY(s->q.ensure(sizeof(double) * ld));
     MBD_TRY(s->scal.ensure(sizeof(double) * 16));
@@ -533,6 +539,7 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     z.v.invb = s->invb.as<double>();
     z.v.length = s->length.as<int>();
     z.v.partial = s->partial.as<double>();
+    z.v.gpartial = s->gpartial.as<double>();
     z.v.counter = s->counter.as<unsigned>();
     return MBD_OK;
 }

@@ -51,42 +51,30 @@ __global__ void __launch_bounds__(256) k_prologue(LanczosView lz, int k, int m, 
         }
     }
     __shared__ double red[8][32];
-    __shared__ bool last;
+    __shared__ double bval[32], tot[32];
     red[ty][lane] = acc;
     __syncthreads();
     if (ty == 0) {
         double s = 0.0;
         for (int w = 0; w < 8; ++w) s += red[w][lane];
-        if (valid) lz.partial[(size_t)blockIdx.x * ld + r] = s;
-        __threadfence();
+        bval[lane] = s;
     }
     __syncthreads();
-    if (lane == 0 && ty == 0) {
-        const unsigned prev = atomicAdd(&lz.counter[blockIdx.y], 1u);
-        last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last && ty == 0) {
-        __threadfence();
-        if (valid) {
-            if (k == 0) {
-                lz.invb[r] = 1.0;
-                lz.length[r] = m;
-            } else {
-                double s = 0.0;
-                for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&lz.partial[(size_t)b * ld + r]);
-                double nrm = sqrt(s);
-                bool active = lz.length[r] == m;
-                if (active && !(nrm > kBreakdown * fabs(lz.a[r]))) {
-                    lz.length[r] = k;
-                    active = false;
-                }
-                if (!active) nrm = 0.0;
-                lz.b[(size_t)(k - 1) * ld + r] = nrm;
-                lz.invb[r] = active ? 1.0 / nrm : 0.0;
+    if (grid_reduce(bval, 32, blockIdx.y * 32, R, ld, lz, tot) && ty == 0 && valid) {
+        if (k == 0) {
+            lz.invb[r] = 1.0;
+            lz.length[r] = m;
+        } else {
+            double nrm = sqrt(tot[lane]);
+            bool active = lz.length[r] == m;
+            if (active && !(nrm > kBreakdown * fabs(lz.a[r]))) {
+                lz.length[r] = k;
+                active = false;
             }
+            if (!active) nrm = 0.0;
+            lz.b[(size_t)(k - 1) * ld + r] = nrm;
+            lz.invb[r] = active ? 1.0 / nrm : 0.0;
         }
-        if (lane == 0) lz.counter[blockIdx.y] = 0u;
     }
 }
 
@@ -158,16 +146,21 @@ __global__ void __launch_bounds__(32) k_tridiag(const double *__restrict__ a, co
                 for (int i = mm - 1; i >= l; --i) {
                     const double f = s * e[i];
                     const double bb = c * e[i];
-                    rr = sqrt(f * f + g * g);
-                    e[i + 1] = rr;
-                    if (rr == 0.0) {
+                    // plane rotation zeroing f against g: r = |(f, g)|, s = f / r, c = g / r,
+                    // with one reciprocal square root (FP64 issue slots are scarce on this GPU)
+                    const double x = fma(f, f, g * g);
+                    if (x == 0.0) {
+                        e[i + 1] = 0.0;
                         d[i + 1] -= p;
                         e[mm] = 0.0;
                         split = true;
                         break;
                     }
-                    s = f / rr;
-                    c = g / rr;
+                    const double inv = rsqrt(x);
+                    rr = x * inv;
+                    e[i + 1] = rr;
+                    s = f * inv;
+                    c = g * inv;
                     g = d[i + 1] - p;
                     rr = (d[i] - g) * s + 2.0 * c * bb;
                     p = s * rr;
@@ -288,29 +281,17 @@ __global__ void __launch_bounds__(256) k_dense_epilogue(int dim, LanczosView lz,
         }
     }
     __shared__ double red[8][32];
-    __shared__ bool last;
+    __shared__ double bval[32], tot[32];
     red[ty][lane] = acc;
     __syncthreads();
     if (ty == 0) {
         double s = 0.0;
         for (int w = 0; w < 8; ++w) s += red[w][lane];
-        if (valid) lz.partial[(size_t)blockIdx.x * ld + r] = s;
-        __threadfence();
+        bval[lane] = s;
     }
     __syncthreads();
-    if (lane == 0 && ty == 0) {
-        const unsigned prev = atomicAdd(&lz.counter[blockIdx.y], 1u);
-        last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last && ty == 0) {
-        __threadfence();
-        double s = 0.0;
-        if (valid)
-            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&lz.partial[(size_t)b * ld + r]);
-        if (valid) lz.a[(size_t)k * ld + r] = s;
-        if (lane == 0) lz.counter[blockIdx.y] = 0u;
-    }
+    if (grid_reduce(bval, 32, blockIdx.y * 32, R, ld, lz, tot) && ty == 0 && valid)
+        lz.a[(size_t)k * ld + r] = tot[lane];
 }
 
 // [nvec][rows] <-> [rows][ld] transposes through a 32x33 shared tile.

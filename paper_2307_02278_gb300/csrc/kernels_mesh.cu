@@ -115,27 +115,74 @@ __global__ void k_scan_add(int *__restrict__ out, const int *__restrict__ bsum, 
     if (i < n) out[i] += bsum[i / 4096];
 }
 
-// D = W^T d: a warp per mesh point, lane = probe (chunk of 32 per blockIdx.y).
-// Columns R..ld-1 (padding of an odd probe count) are written as zeros.
+// D = W^T d.  A warp takes U consecutive mesh points (rows); lane = probe
+// (chunk of 32 per blockIdx.y).  The rows' pointers and their records are
+// fetched with one lane-parallel load each and broadcast by shuffles; the
+// dipole loads of 4 records are issued before they are accumulated.  Rows are
+// summed in record order (fixed), so the result is deterministic.  Columns
+// R..ld-1 (padding of an odd probe count) are written as zeros.
 template <class T>
 __global__ void __launch_bounds__(256) k_spread_csr(const T *__restrict__ d, T *__restrict__ mesh, int R, int ld,
                                                     size_t npts, const int *__restrict__ row,
                                                     const SpreadRec<T> *__restrict__ rec) {
+    constexpr int U = 8;
+    constexpr int B = 4;
+    constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = blockIdx.y * 32 + lane;
     const bool in_ld = r < ld;
     const bool valid = r < R;
-    for (size_t pt = (size_t)blockIdx.x * 8 + warp; pt < npts; pt += (size_t)gridDim.x * 8) {
-        const int q0 = row[pt], q1 = row[pt + 1];
+    const size_t nw = (size_t)gridDim.x * 8;
+    for (size_t pt0 = ((size_t)blockIdx.x * 8 + warp) * U; pt0 < npts; pt0 += nw * U) {
+        int rp = 0;
+        if (lane <= U) rp = row[min(pt0 + lane, npts)];
+        const int qs = __shfl_sync(FULL, rp, 0);
+        const int qe = __shfl_sync(FULL, rp, U);
+        int cur = 0;                                   // row being accumulated (warp-uniform)
+        int next = __shfl_sync(FULL, rp, 1);           // first record of row cur + 1
         T acc = T(0);
-        for (int q = q0; q < q1; ++q) {
-            const SpreadRec<T> w = rec[q];
-            if (valid) {
-                const size_t o = (size_t)(3 * w.atom) * ld + r;
-                acc += w.w0 * d[o] + w.w1 * d[o + ld] + w.w2 * d[o + 2 * (size_t)ld];
+        for (int q0 = qs; q0 < qe; q0 += 32) {
+            SpreadRec<T> mine;
+            mine.w0 = mine.w1 = mine.w2 = T(0);
+            mine.atom = 0;
+            if (q0 + lane < qe) mine = rec[q0 + lane];
+            const int n = min(32, qe - q0);
+            for (int t0 = 0; t0 < n; t0 += B) {
+                T x[B], y[B], z[B], w0[B], w1[B], w2[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int t = min(t0 + u, n - 1);
+                    w0[u] = __shfl_sync(FULL, mine.w0, t);
+                    w1[u] = __shfl_sync(FULL, mine.w1, t);
+                    w2[u] = __shfl_sync(FULL, mine.w2, t);
+                    const int atom = __shfl_sync(FULL, mine.atom, t);
+                    x[u] = y[u] = z[u] = T(0);
+                    if (valid && t0 + u < n) {
+                        const size_t o = (size_t)(3 * atom) * ld + r;
+                        x[u] = d[o];
+                        y[u] = d[o + ld];
+                        z[u] = d[o + 2 * (size_t)ld];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    if (t0 + u < n) {
+                        const int q = q0 + t0 + u;
+                        while (q >= next) {                // row cur is complete
+                            if (in_ld) mesh[(pt0 + cur) * ld + r] = acc;
+                            acc = T(0);
+                            ++cur;
+                            next = __shfl_sync(FULL, rp, cur + 1);
+                        }
+                        acc += w0[u] * x[u] + w1[u] * y[u] + w2[u] * z[u];
+                    }
+                }
             }
         }
-        if (in_ld) mesh[pt * ld + r] = acc;
+        for (; cur < U; ++cur) {
+            if (in_ld && pt0 + cur < npts) mesh[(pt0 + cur) * ld + r] = acc;
+            acc = T(0);
+        }
     }
 }
 
@@ -329,6 +376,128 @@ __global__ void __launch_bounds__(256) k_fft_pass(FFTArgs<T> a) {
     }
 }
 
+// Compile-time specialisation of the pass for common mesh sizes: K, the
+// radix list, the tile width W and every stride are constants, so the index
+// arithmetic folds away and each stage is one unrolled butterfly per thread.
+template <class T, class C, int R, int K, int W, int NS>
+__device__ __forceinline__ void ct_stage(const C *__restrict__ in, C *__restrict__ out, const C *__restrict__ tw,
+                                         int sign) {
+    constexpr int nb = K / R;
+    constexpr int step = K / (NS * R);
+    constexpr int total = nb * W;
+#pragma unroll
+    for (int it = 0; it < (total + 255) / 256; ++it) {
+        const int idx = it * 256 + (int)threadIdx.x;
+        if (total % 256 != 0 && idx >= total) break;
+        const int j = idx / W, col = idx % W;
+        C v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = in[(j + q * nb) * W + col];
+        const int jm = j % NS;
+        if (NS > 1 && jm != 0) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C t = tw[q * jm * step];
+                if (sign > 0) t.y = -t.y;
+                v[q] = cmul(v[q], t);
+            }
+        }
+        dft<T, C, R>(v, sign);
+        const int base = (j / NS) * NS * R + jm;
+#pragma unroll
+        for (int q = 0; q < R; ++q) out[(base + q * NS) * W + col] = v[q];
+    }
+}
+
+template <class T, class C, int K, int W, int NS, int R, int... RS>
+__device__ __forceinline__ C *ct_stages(C *in, C *out, const C *tw, int sign) {
+    ct_stage<T, C, R, K, W, NS>(in, out, tw, sign);
+    __syncthreads();
+    if constexpr (sizeof...(RS) > 0)
+        return ct_stages<T, C, K, W, NS * R, RS...>(out, in, tw, sign);
+    else
+        return out;
+}
+
+template <class T, bool FUSED, int K, int W, int... RS>
+__global__ void __launch_bounds__(256) k_fft_ct(FFTArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_ct[];
+    C *buf[2] = {reinterpret_cast<C *>(smem_ct), reinterpret_cast<C *>(smem_ct) + K * W};
+    C *tw = reinterpret_cast<C *>(smem_ct) + 2 * K * W;
+    for (int i = threadIdx.x; i < K; i += 256) tw[i] = a.tw[i];
+    const int ncb = (a.inner + W - 1) / W;
+    const size_t outer = blockIdx.x / ncb;
+    const int c0 = (int)(blockIdx.x % ncb) * W;
+    const int wc = min(W, a.inner - c0);
+    C *base = a.data + outer * (size_t)K * a.inner + c0;
+#pragma unroll
+    for (int it = 0; it < (K * W + 255) / 256; ++it) {
+        const int idx = it * 256 + (int)threadIdx.x;
+        if ((K * W) % 256 == 0 || idx < K * W) {
+            const int row = idx / W, col = idx % W;
+            buf[0][idx] = col < wc ? base[(size_t)row * a.inner + col] : C{T(0), T(0)};
+        }
+    }
+    __syncthreads();
+    C *res;
+    if (FUSED) {
+        res = ct_stages<T, C, K, W, 1, RS...>(buf[0], buf[1], tw, -1);
+        C *other = (res == buf[0]) ? buf[1] : buf[0];
+        const size_t gstride = (size_t)(a.inner / a.V);
+#pragma unroll
+        for (int it = 0; it < (K * W + 255) / 256; ++it) {
+            const int idx = it * 256 + (int)threadIdx.x;
+            if ((K * W) % 256 == 0 || idx < K * W) {
+                const int row = idx / W, col = idx % W;
+                if (col < wc) {
+                    const T gv = a.G[(size_t)row * gstride + (c0 + col) / a.V];
+                    res[idx].x *= gv;
+                    res[idx].y *= gv;
+                }
+            }
+        }
+        __syncthreads();
+        res = ct_stages<T, C, K, W, 1, RS...>(res, other, tw, +1);
+    } else {
+        res = ct_stages<T, C, K, W, 1, RS...>(buf[0], buf[1], tw, a.sign);
+    }
+#pragma unroll
+    for (int it = 0; it < (K * W + 255) / 256; ++it) {
+        const int idx = it * 256 + (int)threadIdx.x;
+        if ((K * W) % 256 == 0 || idx < K * W) {
+            const int row = idx / W, col = idx % W;
+            if (col < wc) base[(size_t)row * a.inner + col] = res[idx];
+        }
+    }
+}
+
+template <class T, bool FUSED, int K, int W, int... RS>
+bool launch_ct(const FFTArgs<T> &a, unsigned grid, cudaStream_t st) {
+    using C = typename Cplx<T>::type;
+    const size_t smem = sizeof(C) * (2 * (size_t)K * W + K);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_fft_ct<T, FUSED, K, W, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return false;
+    k_fft_ct<T, FUSED, K, W, RS...><<<grid, 256, smem, st>>>(a);
+    return true;
+}
+
+// Launch the specialised pass when K has one; returns false otherwise.
+template <class T, bool FUSED>
+bool launch_fft_ct(const FFTArgs<T> &a, unsigned grid, cudaStream_t st) {
+    constexpr int W = sizeof(T) == 4 ? 32 : 16;
+    if (a.W != W) return false;
+    switch (a.K) {
+        case 32: return launch_ct<T, FUSED, 32, W, 8, 4>(a, grid, st);
+        case 64: return launch_ct<T, FUSED, 64, W, 8, 8>(a, grid, st);
+        case 96: return launch_ct<T, FUSED, 96, W, 8, 4, 3>(a, grid, st);
+        case 128: return launch_ct<T, FUSED, 128, W, 8, 8, 2>(a, grid, st);
+        default: return false;
+    }
+}
+
 // ---------------------------------------------------------------- field
 template <class T> struct FieldArgs {
     const T *d;          // [N][3][ld]
@@ -399,58 +568,63 @@ template <class T, int VEC> __device__ __forceinline__ void vstore(T *p, const T
     }
 }
 
-// One warp per atom; lane owns VEC consecutive probes.  E* = E^rec + E^dir +
-// E^self, then the epilogue selected by o.mode.  P = spline order (0: runtime).
+// Field kernel: one block works on `apb` atoms in turn; for each atom its 8
+// warps split the work (warp w takes stencil planes t1 = w, w + 8, ... and
+// neighbours nb0 + w, nb0 + w + 8, ...; warp 0 adds the self term), lanes own
+// VEC consecutive probes.  The 8 partial fields are summed in a fixed order in
+// shared memory and the epilogue selected by o.mode runs with one thread per
+// probe: E* = E^rec + E^dir + E^self (Eqs. ewalddip, spme, fld_ewald,
+// fld_ewald1), l_k = Omega y_k + Diag(g) E*_k and a_k = y_k^T l_k (Eqs. lk3,
+// recurs2).  PC = spline order (0: runtime).
 template <class T, int VEC, int PC>
-__global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a) {
+__global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a, int apb) {
+    constexpr int NLOC = 32 * VEC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r0 = (blockIdx.y * 32 + lane) * VEC;
+    const int rbase = blockIdx.y * NLOC;
+    const int r0 = rbase + lane * VEC;
     const bool inld = r0 < a.ld;
-    const int idx = blockIdx.x * kWarps + warp;
     const int p = PC > 0 ? PC : a.g.p;
-    double part[VEC];
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) part[v] = 0.0;
-    if (idx < a.g.N && inld) {
+    __shared__ T red[kWarps][3][NLOC];
+    __shared__ double bsum[NLOC];
+    const int tt = threadIdx.x;                 // epilogue probe (tt < NLOC)
+    const int rr = rbase + tt;
+    double part = 0.0;
+    for (int ai = 0; ai < apb; ++ai) {
+        const int idx = blockIdx.x * apb + ai;
+        if (idx >= a.g.N) break;
         const int i = a.order[idx];
         T E0[VEC], E1[VEC], E2[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) E0[v] = E1[v] = E2[v] = T(0);
-        if (a.o.terms & MBD_TERM_RECIP) {
-            T f0[VEC], f1[VEC], f2[VEC];
+        if (inld) {
+            if (a.o.terms & MBD_TERM_RECIP) {
+                T f0[VEC], f1[VEC], f2[VEC];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) f0[v] = f1[v] = f2[v] = T(0);
-            const int top1 = a.sp.top[3 * i], top2 = a.sp.top[3 * i + 1], top3 = a.sp.top[3 * i + 2];
-            const T *w = a.sp.w + (size_t)3 * p * i;
-            const T *dw = a.sp.dw + (size_t)3 * p * i;
-            T wc[PC > 0 ? PC : kMaxOrder], dc[PC > 0 ? PC : kMaxOrder];
-            int k3s[PC > 0 ? PC : kMaxOrder];
+                for (int v = 0; v < VEC; ++v) f0[v] = f1[v] = f2[v] = T(0);
+                const int top1 = a.sp.top[3 * i], top2 = a.sp.top[3 * i + 1], top3 = a.sp.top[3 * i + 2];
+                const T *w = a.sp.w + (size_t)3 * p * i;
+                const T *dw = a.sp.dw + (size_t)3 * p * i;
+                for (int t1 = warp; t1 < p; t1 += kWarps) {
+                    int k1 = top1 - t1;
+                    if (k1 < 0) k1 += a.g.K1;
+                    const T wa = w[t1], da = dw[t1];
 #pragma unroll
-            for (int t3 = 0; t3 < (PC > 0 ? PC : kMaxOrder); ++t3) {
-                if (t3 < p) {
-                    wc[t3] = w[2 * p + t3];
-                    dc[t3] = dw[2 * p + t3];
-                    int k3 = top3 - t3;
-                    if (k3 < 0) k3 += a.g.K3;
-                    k3s[t3] = k3;
-                }
-            }
-            for (int t1 = 0; t1 < p; ++t1) {
-                int k1 = top1 - t1;
-                if (k1 < 0) k1 += a.g.K1;
-                const T wa = w[t1], da = dw[t1];
-                for (int t2 = 0; t2 < p; ++t2) {
-                    int k2 = top2 - t2;
-                    if (k2 < 0) k2 += a.g.K2;
-                    const T wb = w[p + t2], db = dw[p + t2];
-                    const T ab = wa * wb, Ab = da * wb, aB = wa * db;
-                    const T *rowp = a.mesh + ((size_t)k1 * a.g.K2 + k2) * a.g.K3 * a.ld + r0;
+                    for (int t2 = 0; t2 < (PC > 0 ? PC : kMaxOrder); ++t2) {
+                        if (t2 >= p) break;
+                        int k2 = top2 - t2;
+                        if (k2 < 0) k2 += a.g.K2;
+                        const T wb = w[p + t2], db = dw[p + t2];
+                        const T ab = wa * wb, Ab = da * wb, aB = wa * db;
+                        const T *rowp = a.mesh + ((size_t)k1 * a.g.K2 + k2) * a.g.K3 * a.ld + r0;
 #pragma unroll
-                    for (int t3 = 0; t3 < (PC > 0 ? PC : kMaxOrder); ++t3) {
-                        if (t3 < p) {
+                        for (int t3 = 0; t3 < (PC > 0 ? PC : kMaxOrder); ++t3) {
+                            if (t3 >= p) break;
+                            int k3 = top3 - t3;
+                            if (k3 < 0) k3 += a.g.K3;
                             T phi[VEC];
-                            vload<T, VEC>(rowp + (size_t)k3s[t3] * a.ld, phi);
-                            const T c0 = Ab * wc[t3], c1 = aB * wc[t3], c2 = ab * dc[t3];
+                            vload<T, VEC>(rowp + (size_t)k3 * a.ld, phi);
+                            const T wc = w[2 * p + t3], dc = dw[2 * p + t3];
+                            const T c0 = Ab * wc, c1 = aB * wc, c2 = ab * dc;
 #pragma unroll
                             for (int v = 0; v < VEC; ++v) {
                                 f0[v] += c0 * phi[v];
@@ -460,121 +634,109 @@ __global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a) {
                         }
                     }
                 }
-            }
-            // E^rec_alpha = sum_beta C_{beta alpha} f_beta
-            const T m00 = T(a.g.cmat[0]), m01 = T(a.g.cmat[1]), m02 = T(a.g.cmat[2]);
-            const T m10 = T(a.g.cmat[3]), m11 = T(a.g.cmat[4]), m12 = T(a.g.cmat[5]);
-            const T m20 = T(a.g.cmat[6]), m21 = T(a.g.cmat[7]), m22 = T(a.g.cmat[8]);
+                // E^rec_alpha = sum_beta C_{beta alpha} f_beta
+                const T m00 = T(a.g.cmat[0]), m01 = T(a.g.cmat[1]), m02 = T(a.g.cmat[2]);
+                const T m10 = T(a.g.cmat[3]), m11 = T(a.g.cmat[4]), m12 = T(a.g.cmat[5]);
+                const T m20 = T(a.g.cmat[6]), m21 = T(a.g.cmat[7]), m22 = T(a.g.cmat[8]);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                E0[v] += m00 * f0[v] + m10 * f1[v] + m20 * f2[v];
-                E1[v] += m01 * f0[v] + m11 * f1[v] + m21 * f2[v];
-                E2[v] += m02 * f0[v] + m12 * f1[v] + m22 * f2[v];
+                for (int v = 0; v < VEC; ++v) {
+                    E0[v] += m00 * f0[v] + m10 * f1[v] + m20 * f2[v];
+                    E1[v] += m01 * f0[v] + m11 * f1[v] + m21 * f2[v];
+                    E2[v] += m02 * f0[v] + m12 * f1[v] + m22 * f2[v];
+                }
             }
-        }
-        if (a.o.terms & MBD_TERM_REAL) {
-            const int nb0 = a.pr.row[i], nb1 = a.pr.row[i + 1];
-            for (int nb = nb0; nb < nb1; ++nb) {
-                const int j = a.pr.col[nb];
-                const T *A = a.pr.A + 6 * (size_t)nb;
-                const T A0 = A[0], A1 = A[1], A2 = A[2], A3 = A[3], A4 = A[4], A5 = A[5];
+            if (a.o.terms & MBD_TERM_REAL) {
+                const int nb1 = a.pr.row[i + 1];
+                constexpr int B4 = 4;
+                for (int nb = a.pr.row[i] + warp; nb < nb1; nb += B4 * kWarps) {
+                    int jj[B4];
+#pragma unroll
+                    for (int u = 0; u < B4; ++u) jj[u] = (nb + u * kWarps < nb1) ? a.pr.col[nb + u * kWarps] : -1;
+                    T xs[B4][VEC], ys[B4][VEC], zs[B4][VEC];
+#pragma unroll
+                    for (int u = 0; u < B4; ++u) {
+                        if (jj[u] >= 0) {
+                            const T *dj = a.d + (size_t)(3 * jj[u]) * a.ld + r0;
+                            vload<T, VEC>(dj, xs[u]);
+                            vload<T, VEC>(dj + a.ld, ys[u]);
+                            vload<T, VEC>(dj + 2 * (size_t)a.ld, zs[u]);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < B4; ++u) {
+                        if (jj[u] >= 0) {
+                            const T *A = a.pr.A + 6 * (size_t)(nb + u * kWarps);
+                            const T A0 = A[0], A1 = A[1], A2 = A[2], A3 = A[3], A4 = A[4], A5 = A[5];
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                E0[v] += A0 * xs[u][v] + A1 * ys[u][v] + A2 * zs[u][v];
+                                E1[v] += A1 * xs[u][v] + A3 * ys[u][v] + A4 * zs[u][v];
+                                E2[v] += A2 * xs[u][v] + A4 * ys[u][v] + A5 * zs[u][v];
+                            }
+                        }
+                    }
+                }
+            }
+            if ((a.o.terms & MBD_TERM_SELF) && warp == 0) {
+                const T c = T(a.self_coef);
                 T x[VEC], y[VEC], z[VEC];
-                const T *dj = a.d + (size_t)(3 * j) * a.ld + r0;
-                vload<T, VEC>(dj, x);
-                vload<T, VEC>(dj + a.ld, y);
-                vload<T, VEC>(dj + 2 * (size_t)a.ld, z);
+                const T *di = a.d + (size_t)(3 * i) * a.ld + r0;
+                vload<T, VEC>(di, x);
+                vload<T, VEC>(di + a.ld, y);
+                vload<T, VEC>(di + 2 * (size_t)a.ld, z);
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
-                    E0[v] += A0 * x[v] + A1 * y[v] + A2 * z[v];
-                    E1[v] += A1 * x[v] + A3 * y[v] + A4 * z[v];
-                    E2[v] += A2 * x[v] + A4 * y[v] + A5 * z[v];
+                    E0[v] += c * x[v];
+                    E1[v] += c * y[v];
+                    E2[v] += c * z[v];
                 }
             }
         }
-        if (a.o.terms & MBD_TERM_SELF) {
-            const T c = T(a.self_coef);
-            T x[VEC], y[VEC], z[VEC];
-            const T *di = a.d + (size_t)(3 * i) * a.ld + r0;
-            vload<T, VEC>(di, x);
-            vload<T, VEC>(di + a.ld, y);
-            vload<T, VEC>(di + 2 * (size_t)a.ld, z);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                E0[v] += c * x[v];
-                E1[v] += c * y[v];
-                E2[v] += c * z[v];
-            }
+        for (int v = 0; v < VEC; ++v) {
+            red[warp][0][lane * VEC + v] = E0[v];
+            red[warp][1][lane * VEC + v] = E1[v];
+            red[warp][2][lane * VEC + v] = E2[v];
         }
-        const size_t o0 = (size_t)(3 * i) * a.ld + r0;
-        const T *Ec[3] = {E0, E1, E2};
-        if (a.o.mode == kFieldOut) {
+        __syncthreads();
+        if (tt < NLOC && rr < a.ld) {
+            double E[3];
             for (int c = 0; c < 3; ++c) {
-                double e[VEC];
+                T s = T(0);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) e[v] = double(Ec[c][v]);
-                vstore<double, VEC>(a.o.out + o0 + (size_t)c * a.ld, e);
+                for (int w = 0; w < kWarps; ++w) s += red[w][c][tt];
+                E[c] = double(s);
             }
-        } else if (a.o.mode == kFieldApply) {
-            const double w2 = a.w2[i], gi = a.g_at[i];
-            for (int c = 0; c < 3; ++c) {
-                double x[VEC], y[VEC];
-                vload<double, VEC>(a.o.xin + o0 + (size_t)c * a.ld, x);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) y[v] = w2 * x[v] + gi * double(Ec[c][v]);
-                vstore<double, VEC>(a.o.out + o0 + (size_t)c * a.ld, y);
-            }
-        } else {
-            double invb[VEC];
-            vload<double, VEC>(a.o.lz.invb + r0, invb);
-            const double w2 = a.w2[i], gi = a.g_at[i];
-            double *Yk = a.o.lz.Y + (size_t)a.o.k * (size_t)(3 * a.g.N) * a.ld;
-            for (int c = 0; c < 3; ++c) {
-                double ys[VEC], y[VEC], l[VEC];
-                vload<double, VEC>(Yk + o0 + (size_t)c * a.ld, ys);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    y[v] = ys[v] * invb[v];
-                    l[v] = w2 * y[v] + gi * double(Ec[c][v]) * invb[v];
-                    part[v] += y[v] * l[v];
+            const size_t o0 = (size_t)(3 * i) * a.ld + rr;
+            if (a.o.mode == kFieldOut) {
+                for (int c = 0; c < 3; ++c) a.o.out[o0 + (size_t)c * a.ld] = E[c];
+            } else if (a.o.mode == kFieldApply) {
+                const double w2 = a.w2[i], gi = a.g_at[i];
+                for (int c = 0; c < 3; ++c)
+                    a.o.out[o0 + (size_t)c * a.ld] = w2 * a.o.xin[o0 + (size_t)c * a.ld] + gi * E[c];
+            } else {
+                const double invb = a.o.lz.invb[rr];
+                const double w2 = a.w2[i], gi = a.g_at[i];
+                double *Yk = a.o.lz.Y + (size_t)a.o.k * (size_t)(3 * a.g.N) * a.ld;
+                for (int c = 0; c < 3; ++c) {
+                    const double y = Yk[o0 + (size_t)c * a.ld] * invb;
+                    const double l = w2 * y + gi * E[c] * invb;
+                    Yk[o0 + (size_t)c * a.ld] = y;
+                    a.o.lz.L[o0 + (size_t)c * a.ld] = l;
+                    part += y * l;
                 }
-                vstore<double, VEC>(Yk + o0 + (size_t)c * a.ld, y);
-                vstore<double, VEC>(a.o.lz.L + o0 + (size_t)c * a.ld, l);
             }
         }
+        __syncthreads();
     }
     if (a.o.mode != kFieldLanczos) return;
-    // a_k = y_k^T l_k: block partial per probe, then the last block sums the
-    // partials in block order (deterministic) and resets the counter.
-    __shared__ double red[kWarps][32 * VEC];
-    __shared__ bool last;
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) red[warp][lane * VEC + v] = part[v];
+    // a_k = y_k^T l_k: deterministic reduction over blocks
+    if (tt < NLOC) bsum[tt] = part;
     __syncthreads();
-    const int nloc = 32 * VEC;
-    const int rbase = blockIdx.y * nloc;
-    for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < kWarps; ++w) s += red[w][t];
-        if (rbase + t < a.R) a.o.lz.partial[(size_t)blockIdx.x * a.ld + rbase + t] = s;
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(&a.o.lz.counter[blockIdx.y], 1u);
-        last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        for (int t = threadIdx.x; t < nloc; t += blockDim.x) {
-            const int r = rbase + t;
-            if (r < a.R) {
-                double s = 0.0;
-                for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&a.o.lz.partial[(size_t)b * a.ld + r]);
-                a.o.lz.a[(size_t)a.o.k * a.ld + r] = s;
-            }
-        }
-        if (threadIdx.x == 0) a.o.lz.counter[blockIdx.y] = 0u;
+    __shared__ double tot[NLOC];
+    if (grid_reduce(bsum, NLOC, rbase, a.R, a.ld, a.o.lz, tot)) {
+        for (int k = threadIdx.x; k < NLOC; k += blockDim.x)
+            if (rbase + k < a.R) a.o.lz.a[(size_t)a.o.k * a.ld + rbase + k] = tot[k];
     }
 }
 
@@ -636,7 +798,7 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s) {
 template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, int R, int ld) {
     PrecData<T> &P = prec<T>(s);
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
-    const unsigned gx = (unsigned)std::min<size_t>((npts + 7) / 8, 152 * 64);
+    const unsigned gx = (unsigned)std::min<size_t>((npts + 63) / 64, 152 * 16);
     dim3 grid(gx, (ld + 31) / 32);
     k_spread_csr<T><<<grid, 256, 0, s->stream>>>(d, mesh, R, ld, npts, P.srow.template as<int>(),
                                                  P.srec.template as<SpreadRec<T>>());
@@ -665,6 +827,10 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld) {
         a.sign = sign;
         const size_t smem = sizeof(C) * (2 * (size_t)a.K * a.W + a.K);
         dim3 grid((unsigned)((size_t)outer * ((inner + a.W - 1) / a.W)));
+        if (fused ? launch_fft_ct<T, true>(a, grid.x, s->stream) : launch_fft_ct<T, false>(a, grid.x, s->stream)) {
+            MBD_LAUNCH_CHECK();
+            return MBD_OK;
+        }
         if (fused) {
             if (smem > 48 * 1024)
                 MBD_CUDA_TRY(cudaFuncSetAttribute(k_fft_pass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -704,8 +870,9 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     a.self_coef = -4.0 * s->ewald_beta * s->ewald_beta * s->ewald_beta / (3.0 * 1.77245385090551602730);
     a.o = o;
     const int vec = (sizeof(T) == 4 && ld % 4 == 0 && ld >= 128) ? 4 : ((ld % 2 == 0 && ld >= 64) ? 2 : 1);
-    dim3 grid((s->N + kWarps - 1) / kWarps, (ld + 32 * vec - 1) / (32 * vec));
-#define MBD_FIELD_LAUNCH(V, P) k_field<T, V, P><<<grid, kWarps * 32, 0, s->stream>>>(a)
+    const int apb = field_apb(s->N);
+    dim3 grid(field_blocks(s->N), (ld + 32 * vec - 1) / (32 * vec));
+#define MBD_FIELD_LAUNCH(V, P) k_field<T, V, P><<<grid, kWarps * 32, 0, s->stream>>>(a, apb)
     if (vec == 4) {
         if constexpr (sizeof(T) == 4) {
             if (s->p == 6) MBD_FIELD_LAUNCH(4, 6);
@@ -723,7 +890,9 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     return MBD_OK;
 }
 
-int field_blocks(int N) { return (N + kWarps - 1) / kWarps; }
+// Atoms per block of the field kernel: about four blocks per SM.
+int field_apb(int N) { return std::max(1, std::min(64, (N + 152 * 4 - 1) / (152 * 4))); }
+int field_blocks(int N) { return (N + field_apb(N) - 1) / field_apb(N); }
 
 template mbd_status build_spread_matrix<double>(mbd_system *);
 template mbd_status build_spread_matrix<float>(mbd_system *);

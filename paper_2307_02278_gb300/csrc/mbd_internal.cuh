@@ -103,8 +103,62 @@ struct LanczosView {
     double *invb;       // [ld]     1/b for the current step (0 after breakdown)
     int *length;        // [ld]     Krylov length per probe (m unless broken down)
     double *partial;    // [nblk][ld] block partial sums
-    unsigned *counter;  // [nchunk] last-block counters (self-resetting)
+    double *gpartial;   // [ngroups][ld] group sums (two-level reduction)
+    unsigned *counter;  // [nchunk][cstride] last-block counters (self-resetting)
+    int cstride;        // counters per probe chunk (>= ngroups + 1)
 };
+
+// Deterministic two-level reduction across the blocks of a grid row
+// (blockIdx.y = probe chunk).  Each block contributes bval[t] for the probes
+// rbase + t (t < nloc); blocks are grouped by kRedGroup; the last block of a
+// group sums its group in block order, the last group finisher sums the groups
+// in group order.  Returns true (block-uniformly) in exactly one block, whose
+// out[t] then holds the grid totals.  Counters reset themselves.
+constexpr int kRedGroup = 16;
+__device__ __forceinline__ bool grid_reduce(const double *bval, int nloc, int rbase, int R, int ld,
+                                            const LanczosView &lz, double *out) {
+    __shared__ bool s_last;
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const unsigned nblk = gridDim.x;
+    const unsigned ngroups = (nblk + kRedGroup - 1) / kRedGroup;
+    unsigned *cnt = lz.counter + (size_t)blockIdx.y * lz.cstride;
+    for (int k = t; k < nloc; k += nthr)
+        if (rbase + k < R) lz.partial[(size_t)blockIdx.x * ld + rbase + k] = bval[k];
+    __threadfence();
+    __syncthreads();
+    const unsigned g = blockIdx.x / kRedGroup;
+    const unsigned gsize = min((unsigned)kRedGroup, nblk - g * kRedGroup);
+    if (t == 0) s_last = (atomicAdd(&cnt[g], 1u) == gsize - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int k = t; k < nloc; k += nthr) {
+        const int r = rbase + k;
+        if (r < R) {
+            double s = 0.0;
+            for (unsigned b = g * kRedGroup; b < g * kRedGroup + gsize; ++b) s += __ldcg(&lz.partial[(size_t)b * ld + r]);
+            lz.gpartial[(size_t)g * ld + r] = s;
+        }
+    }
+    if (t == 0) cnt[g] = 0u;
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = (atomicAdd(&cnt[ngroups], 1u) == ngroups - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int k = t; k < nloc; k += nthr) {
+        const int r = rbase + k;
+        double s = 0.0;
+        if (r < R)
+            for (unsigned gg = 0; gg < ngroups; ++gg) s += __ldcg(&lz.gpartial[(size_t)gg * ld + r]);
+        out[k] = s;
+    }
+    if (t == 0) cnt[ngroups] = 0u;
+    __syncthreads();
+    return true;
+}
 
 // ---------------------------------------------------------------- per-system state
 struct SystemData;
@@ -174,7 +228,8 @@ struct mbd_system {
     mbd::PrecData<double> f64;
     mbd::PrecData<float> f32;
     // Lanczos workspace
-    mbd::DevBuf Y, L, a, b, invb, length, partial, counter, q, scal, status, work, work2;
+    mbd::DevBuf Y, L, a, b, invb, length, partial, gpartial, counter, q, scal, status, work, work2;
+    int counter_stride = 0;
     mbd::DevBuf forces_acc;
     mbd::Profiler prof;
     // pinned host staging
@@ -217,6 +272,7 @@ mbd_status launch_probes(uint64_t seed, int first, int R, int dim, double *v, cu
 mbd_status launch_dense_step(const double *c, int dim, const LanczosView &lz, int k, int R, int ld, int nblk,
                              cudaStream_t st);
 int field_blocks(int N);
+int field_apb(int N);
 
 // layout helpers
 mbd_status launch_to_probe_major(const double *x, int nvec, int rows, double *xt, int ld, cudaStream_t st);
