@@ -43,6 +43,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--eigen", default="fp64", choices=["fp64", "df64"],
+                    help="arithmetic of the tridiagonal eigensolve (fp64 default)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -253,7 +255,7 @@ def run_ours(args, world, rank, local):
     R, m = s.n_probes, s.n_steps
     seed = (s.probe_seed + ((rank * R) << 32)) % (1 << 64)
     stream = torch.cuda.Stream()
-    sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, stream=stream)
+    sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, eigen_precision=args.eigen, stream=stream)
     info = sysm.info()
     forces = torch.empty((s.n_atoms, 3), dtype=torch.float64, device="cuda")
     energy_t = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -397,7 +399,8 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh),
                        "spline_order": s.spline_order, "n_probes_per_gpu": R, "n_steps": m,
-                       "precision": args.precision, "ewald_beta": s.ewald_beta, "r_cut": s.r_cut,
+                       "precision": args.precision, "eigensolve": args.eigen, "ewald_beta": s.ewald_beta,
+                       "r_cut": s.r_cut,
                        "n_pairs": info["n_pairs"], "step": "mbd_energy_forces (energy + forces)",
                        "l2": "flushed before every timed step (512 MB write, outside the events)",
                        "parallelism": f"probes sharded over {world} GPU(s)"},

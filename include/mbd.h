@@ -60,6 +60,13 @@ typedef enum {
  * eigensolve and the trace sum are always FP64. */
 enum { MBD_FP64 = 0, MBD_MIXED = 1 /* FP32 operator, FP64 Lanczos */ };
 
+/* Arithmetic of the small tridiagonal eigensolve (Eq. tridiag2).  FP64 is the
+ * default.  MBD_EIGEN_DF64 runs the same implicit-QL algorithm in double-float
+ * arithmetic (pairs of FP32 numbers, 48-bit significand; quadrature values
+ * agree with FP64 to about 1e-13 relative), several times faster on GPUs whose
+ * FP64 issue rate is a small fraction of FP32. */
+enum { MBD_EIGEN_FP64 = 0, MBD_EIGEN_DF64 = 1 };
+
 /* Field terms for mbd_field (bit mask). */
 enum { MBD_TERM_REAL = 1, MBD_TERM_RECIP = 2, MBD_TERM_SELF = 4, MBD_TERM_ALL = 7 };
 
@@ -87,6 +94,7 @@ typedef struct {
     int32_t mesh[3];          /* K_alpha: products of 2, 3, 5 only; 2p <= K_alpha <= 1000 */
     int32_t spline_order;     /* p: even, 4 <= p <= 10 */
     int32_t precision;        /* MBD_FP64 or MBD_MIXED */
+    int32_t eigen_precision;  /* MBD_EIGEN_FP64 (default) or MBD_EIGEN_DF64 */
 } mbd_system_desc;
 
 /* Create a system: validate, upload, build the neighbour list, spline

@@ -19,6 +19,7 @@ STATUS = {
     7: "MBD_ERR_UNSUPPORTED", 8: "MBD_ERR_NO_DEVICE",
 }
 MBD_FP64, MBD_MIXED = 0, 1
+MBD_EIGEN_FP64, MBD_EIGEN_DF64 = 0, 1
 MBD_TERM_REAL, MBD_TERM_RECIP, MBD_TERM_SELF, MBD_TERM_ALL = 1, 2, 4, 7
 
 
@@ -38,6 +39,7 @@ class SystemDesc(ctypes.Structure):
         ("mesh", c_int32 * 3),
         ("spline_order", c_int32),
         ("precision", c_int32),
+        ("eigen_precision", c_int32),
     ]
 
 

@@ -163,6 +163,7 @@ mbd_status validate(const mbd_system_desc *d) {
         if (d->mesh[a] < 2 * p || d->mesh[a] > 1000 || !factor_mesh(d->mesh[a], f)) return MBD_ERR_INVALID_ARG;
     }
     if (d->precision != MBD_FP64 && d->precision != MBD_MIXED) return MBD_ERR_INVALID_ARG;
+    if (d->eigen_precision != MBD_EIGEN_FP64 && d->eigen_precision != MBD_EIGEN_DF64) return MBD_ERR_INVALID_ARG;
     return MBD_OK;
 }
 
@@ -441,6 +442,7 @@ mbd_status create_impl(const mbd_system_desc *d, void *stream, mbd_system **out)
     s->damp_beta = d->damp_beta;
     s->damp_d = d->damp_d;
     s->precision = d->precision;
+    s->eigen_df64 = d->eigen_precision == MBD_EIGEN_DF64 ? 1 : 0;
     s->stream = static_cast<cudaStream_t>(stream);
     const size_t n = (size_t)s->N;
     s->alpha.assign(d->alpha, d->alpha + n);
@@ -505,7 +507,7 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     z.ld = probe_ld(R);
     z.m = m;
     z.rows = rows;
-    z.nblk = std::max(1, std::min((rows + 63) / 64, 2048));
+    z.nblk = std::max(1, std::min((rows + 15) / 16, 4096));
     const size_t ld = z.ld;
     const int nchunk = (z.ld + 31) / 32;
     MBD_TRY(s->Y.ensure(sizeof(double) * (size_t)m * rows * ld));
@@ -564,13 +566,22 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
     fo.out = nullptr;
     fo.xin = nullptr;
     fo.lz = z.v;
+    // the fused spread + k3 pass exists for the specialised sizes with whole probe-pair tiles
+    const bool fuse3 = (s->K[2] == 32 || s->K[2] == 64 || s->K[2] == 96 || s->K[2] == 128) &&
+                       ((z.ld / 2) % (sizeof(T) == 4 ? 32 : 16) == 0) && s->K[0] * s->K[1] > 0;
     for (int k = 0; k < m; ++k) {
         MBD_STAGE(s, MBD_STAGE_PROLOGUE, 1,
                   launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
                                     (int)sizeof(T), z.nblk));
-        MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
-                  launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
-        MBD_STAGE(s, MBD_STAGE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld));
+        if (fuse3) {
+            MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
+                      launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
+            MBD_STAGE(s, MBD_STAGE_FFT, 4, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld, true));
+        } else {
+            MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
+                      launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
+            MBD_STAGE(s, MBD_STAGE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld));
+        }
         fo.k = k;
         MBD_STAGE(s, MBD_STAGE_FIELD, 1,
                   launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
@@ -578,7 +589,8 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
     if (full) MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
               launch_tridiag(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(),
-                             full ? s->work2.as<double>() : nullptr, s->status.as<int>(), s->stream));
+                             full ? s->work2.as<double>() : nullptr, s->status.as<int>(), s->stream,
+                             s->eigen_df64 != 0));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
               launch_energy_reduce(s->q.as<double>(), R, rows, s->omega_sum, s->scal.as<double>(), s->stream));
     return MBD_OK;
@@ -647,9 +659,17 @@ mbd_status forces_impl(mbd_system *s, int R, int m, uint64_t seed, double *energ
     MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
               launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m,
                                         P.d.template as<T>(), ld2));
-    MBD_STAGE(s, MBD_STAGE_FORCE_SPREAD, 1,
-              launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));
-    MBD_STAGE(s, MBD_STAGE_FORCE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), ld2));
+    const bool fuse3 = (s->K[2] == 32 || s->K[2] == 64 || s->K[2] == 96 || s->K[2] == 128) &&
+                       ((ld2 / 2) % (sizeof(T) == 4 ? 32 : 16) == 0);
+    if (fuse3) {
+        MBD_STAGE(s, MBD_STAGE_FORCE_SPREAD, 1,
+                  launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));
+        MBD_STAGE(s, MBD_STAGE_FORCE_FFT, 4, launch_convolve<T>(s, P.mesh.template as<T>(), ld2, true));
+    } else {
+        MBD_STAGE(s, MBD_STAGE_FORCE_SPREAD, 1,
+                  launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));
+        MBD_STAGE(s, MBD_STAGE_FORCE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), ld2));
+    }
     const double scale = 0.25 * (3.0 * s->N) / R;
     MBD_STAGE(s, MBD_STAGE_FORCE_GATHER, 1,
               launch_force_gather_t<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, ld2, scale,
@@ -864,6 +884,7 @@ mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double ome
     if (!s) return MBD_ERR_OOM;
     s->N = (dim + 2) / 3;
     s->stream = nullptr;
+    s->eigen_df64 = 0;
     s->omega_sum = omega_sum;
     auto run = [&]() -> mbd_status {
         if (cudaMallocHost(&s->host_scal, 16 * sizeof(double)) != cudaSuccess) return MBD_ERR_OOM;

@@ -3,6 +3,7 @@
 // (Eq. recurs2, Algorithm 2), the tridiagonal Gauss quadrature (Eqs. tridiag2,
 // sl3, sl4) and the trace/energy reduction (Eq. plasmonic2, Algorithm 1).
 #include "mbd_internal.cuh"
+#include "ql.cuh"
 
 namespace mbd {
 
@@ -78,149 +79,136 @@ __global__ void __launch_bounds__(256) k_prologue(LanczosView lz, int k, int m, 
     }
 }
 
-// Gauss quadrature of one probe's tridiagonal Delta (Eqs. tridiag2, sl3): a
-// warp per probe.  Implicit QL with Wilkinson shifts (Bowdler, Martin, Reinsch
-// & Wilkinson 1968): lane 0 runs the scalar chain of each sweep in shared
-// memory and records the plane rotations; then every lane applies them to its
-// rows of U (initially I).  The Gauss weights are U_1k^2 (Golub & Welsch
-// 1969), so without FULL only row 1 of U is kept.  With FULL the whole U is
-// kept and c = Delta^{-1/2} e_1 = U diag(theta^{-1/2}) U^T e_1 is returned as
-// well (w = C^{-1/2} v = sum_k c_k y_k for the force estimator).
+// Gauss quadrature of one probe's tridiagonal Delta (Eqs. tridiag2, sl3) by
+// implicit QL (ql.cuh), one block of two warps per probe.  Warp 0 runs the
+// sweeps (their scalar chain on lane 0) and records each sweep's rotations;
+// warp 1 applies the previous sweep's rotations to the rows of U (I at the
+// start) at the same time: rotations are double-buffered, one barrier per
+// sweep.  The Gauss weights are U_1k^2, so without FULL only row 1 of U is
+// kept; with FULL the whole U is kept and c = Delta^{-1/2} e_1 =
+// U diag(theta^{-1/2}) U^T e_1 is returned as well (w = C^{-1/2} v =
+// sum_k c_k y_k for the force estimator).  S = double (FP64) or df.
 // status bit 1: a Ritz value <= 0; bit 2: a sweep limit hit; bit 4: NaN/Inf.
-template <bool FULL>
-__global__ void __launch_bounds__(32) k_tridiag(const double *__restrict__ a, const double *__restrict__ b,
+template <class S, bool FULL>
+__global__ void __launch_bounds__(64) k_tridiag(const double *__restrict__ a, const double *__restrict__ b,
                                                 const int *__restrict__ length, int R, int ld, int m,
                                                 double *__restrict__ q, double *__restrict__ coef,
                                                 int *__restrict__ status) {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    S *d = reinterpret_cast<S *>(sm_raw);
+    S *e = d + m;
+    S *cs = e + m;          // [2][m]
+    S *sn = cs + 2 * m;     // [2][m]
+    S *Z = sn + 2 * m;      // [nz][n + 1]
+    __shared__ int s_mm[2], s_nrot[2], s_done, s_bad;
+    __shared__ double s_part[2];
+    __shared__ int s_neg[2];
     const int r = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (r >= R) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = length ? length[r] : m;
-    const int zs = n + 1;                   // padded row stride of U (bank-conflict free)
-    double *d = sm, *e = sm + m, *cs = sm + 2 * m, *sn = sm + 3 * m, *Z = sm + 4 * m;
-    __shared__ int s_nrot, s_bad;
-    bool finite = true;
-    for (int k = lane; k < n; k += 32) {
-        d[k] = a[(size_t)k * ld + r];
-        e[k] = (k < n - 1) ? b[(size_t)k * ld + r] : 0.0;
-        finite = finite && isfinite(d[k]) && isfinite(e[k]);
-    }
+    const int zs = n + 1;
     const int nz = FULL ? n : 1;
-    for (int row = lane; row < nz; row += 32)
-        for (int col = 0; col < n; ++col) Z[row * zs + col] = (row == col) ? 1.0 : 0.0;
-    if (lane == 0) s_bad = 0;
-    finite = __all_sync(0xffffffffu, finite);
-    __syncwarp();
+    int finite = 1;
+    for (int k2 = tid; k2 < n; k2 += 64) {
+        const double dv = a[(size_t)k2 * ld + r];
+        const double ev = (k2 < n - 1) ? b[(size_t)k2 * ld + r] : 0.0;
+        finite &= (isfinite(dv) && isfinite(ev)) ? 1 : 0;
+        to_scalar(dv, d[k2]);
+        to_scalar(ev, e[k2]);
+    }
+    for (int row = tid; row < nz; row += 64)
+        for (int col = 0; col < n; ++col) to_scalar(row == col ? 1.0 : 0.0, Z[row * zs + col]);
+    if (tid == 0) {
+        s_done = 0;
+        s_bad = 0;
+        s_nrot[0] = s_nrot[1] = 0;
+    }
+    finite = __syncthreads_and(finite);
     if (!finite) {
-        if (lane == 0) {
+        if (tid == 0) {
             atomicOr(status, 4);
             q[r] = 0.0;
         }
         if (FULL)
-            for (int k = lane; k < m; k += 32) coef[(size_t)k * ld + r] = 0.0;
+            for (int k2 = tid; k2 < m; k2 += 64) coef[(size_t)k2 * ld + r] = 0.0;
         return;
     }
-    const double eps = 2.220446049250313e-16;
-    for (int l = 0; l < n; ++l) {
-        int iter = 0;
-        for (;;) {
-            int mm = l;
-            for (; mm < n - 1; ++mm) {
-                const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
-                if (fabs(e[mm]) <= eps * dd) break;
-            }
-            if (mm == l) break;
-            if (++iter > 60) {
-                if (lane == 0) s_bad = 1;
-                break;
-            }
-            __syncwarp();   // every lane has read d, e before lane 0 rewrites them
-            if (lane == 0) {
-                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-                double rr = sqrt(g * g + 1.0);
-                g = d[mm] - d[l] + e[l] / (g + copysign(rr, g));
-                double s = 1.0, c = 1.0, p = 0.0;
-                int nrot = 0;
-                bool split = false;
-                for (int i = mm - 1; i >= l; --i) {
-                    const double f = s * e[i];
-                    const double bb = c * e[i];
-                    // plane rotation zeroing f against g: r = |(f, g)|, s = f / r, c = g / r,
-                    // with one reciprocal square root (FP64 issue slots are scarce on this GPU)
-                    const double x = fma(f, f, g * g);
-                    if (x == 0.0) {
-                        e[i + 1] = 0.0;
-                        d[i + 1] -= p;
-                        e[mm] = 0.0;
-                        split = true;
-                        break;
-                    }
-                    const double inv = rsqrt(x);
-                    rr = x * inv;
-                    e[i + 1] = rr;
-                    s = f * inv;
-                    c = g * inv;
-                    g = d[i + 1] - p;
-                    rr = (d[i] - g) * s + 2.0 * c * bb;
-                    p = s * rr;
-                    d[i + 1] = g + p;
-                    g = c * rr - bb;
-                    cs[i] = c;
-                    sn[i] = s;
-                    ++nrot;
+    int l = 0, iter = 0;        // warp-0 state (identical in its lanes)
+    for (int t = 0;; ++t) {
+        const int buf = t & 1;
+        if (warp == 0) {
+            bool produced = false;
+            while (l < n && !produced) {
+                const int mm = find_split(d, e, l, n);
+                if (mm == l) {
+                    ++l;
+                    iter = 0;
+                    continue;
                 }
-                if (!split) {
-                    d[l] -= p;
-                    e[l] = g;
-                    e[mm] = 0.0;
+                if (++iter > 60) {
+                    if (lane == 0) s_bad = 1;
+                    l = n;
+                    break;
                 }
-                s_nrot = nrot;
-            }
-            __syncwarp();
-            const int nrot = s_nrot;
-            for (int row = lane; row < nz; row += 32) {
-                double *zr = Z + row * zs;
-                for (int t = 0; t < nrot; ++t) {
-                    const int i = mm - 1 - t;
-                    const double zf = zr[i + 1];
-                    zr[i + 1] = sn[i] * zr[i] + cs[i] * zf;
-                    zr[i] = cs[i] * zr[i] - sn[i] * zf;
+                __syncwarp();   // every lane has read d, e before lane 0 rewrites them
+                if (lane == 0) {
+                    int nrot = ql_sweep(d, e, cs + buf * m, sn + buf * m, l, mm);
+                    if (nrot < 0) nrot = -nrot - 1;
+                    s_nrot[buf] = nrot;
+                    s_mm[buf] = mm;
                 }
+                __syncwarp();
+                produced = true;
             }
-            __syncwarp();
+            if (!produced && lane == 0) {
+                s_nrot[buf] = 0;
+                s_done = 1;
+            }
+        } else if (t > 0) {
+            const int pb = buf ^ 1;
+            const int nrot = s_nrot[pb], mm = s_mm[pb];
+            if (nrot > 0)
+                for (int row = lane; row < nz; row += 32)
+                    apply_rotations(Z + row * zs, cs + pb * m, sn + pb * m, mm, nrot);
         }
-        __syncwarp();
-        if (s_bad) break;
+        __syncthreads();
+        if (s_done) break;      // the last sweep was applied in this round
     }
-    __syncwarp();
     // q = sum_k U_1k^2 sqrt(theta_k)
     double part = 0.0;
-    bool pos = true;
-    for (int k = lane; k < n; k += 32) {
-        const double th = d[k];
+    int neg = 0;
+    for (int k2 = tid; k2 < n; k2 += 64) {
+        const double th = from_scalar(d[k2]);
+        const double z0 = from_scalar(Z[k2]);
         if (th > 0.0)
-            part += Z[k] * Z[k] * sqrt(th);
+            part += z0 * z0 * sqrt(th);
         else
-            pos = false;
+            neg = 1;
     }
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-    pos = __all_sync(0xffffffffu, pos);
+    for (int off = 16; off > 0; off >>= 1) {
+        part += __shfl_down_sync(0xffffffffu, part, off);
+        neg |= __shfl_down_sync(0xffffffffu, neg, off);
+    }
     if (lane == 0) {
-        q[r] = part;
-        if (!pos) atomicOr(status, 1);
+        s_part[warp] = part;
+        s_neg[warp] = neg;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        q[r] = s_part[0] + s_part[1];
+        if (s_neg[0] | s_neg[1]) atomicOr(status, 1);
         if (s_bad) atomicOr(status, 2);
     }
     if (FULL) {
         // c_k = sum_j U_kj theta_j^{-1/2} U_1j
-        for (int k = lane; k < m; k += 32) {
+        for (int k2 = tid; k2 < m; k2 += 64) {
             double c = 0.0;
-            if (k < n)
+            if (k2 < n)
                 for (int j = 0; j < n; ++j) {
-                    const double th = d[j];
-                    if (th > 0.0) c += Z[k * zs + j] * Z[j] / sqrt(th);
+                    const double th = from_scalar(d[j]);
+                    if (th > 0.0) c += from_scalar(Z[k2 * zs + j]) * from_scalar(Z[j]) * rsqrt(th);
                 }
-            coef[(size_t)k * ld + r] = c;
+            coef[(size_t)k2 * ld + r] = c;
         }
     }
 }
@@ -363,19 +351,26 @@ mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int 
     return MBD_OK;
 }
 
-mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
-                          double *coef, int *status, cudaStream_t st) {
+template <class S>
+mbd_status launch_tridiag_s(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
+                            double *coef, int *status, cudaStream_t st) {
     const bool full = coef != nullptr;
-    const size_t smem = sizeof(double) * (size_t)(4 * m + (full ? m * (m + 1) : m));
+    const size_t smem = sizeof(S) * (size_t)(6 * m + (full ? m * (m + 1) : m + 1));
     if (full) {
         if (smem > 48 * 1024)
-            MBD_CUDA_TRY(cudaFuncSetAttribute(k_tridiag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_tridiag<true><<<R, 32, smem, st>>>(a, b, length, R, ld, m, q, coef, status);
+            MBD_CUDA_TRY(cudaFuncSetAttribute(k_tridiag<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_tridiag<S, true><<<R, 64, smem, st>>>(a, b, length, R, ld, m, q, coef, status);
     } else {
-        k_tridiag<false><<<R, 32, smem, st>>>(a, b, length, R, ld, m, q, nullptr, status);
+        k_tridiag<S, false><<<R, 64, smem, st>>>(a, b, length, R, ld, m, q, nullptr, status);
     }
     MBD_LAUNCH_CHECK();
     return MBD_OK;
+}
+
+mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
+                          double *coef, int *status, cudaStream_t st, bool df64) {
+    if (df64) return launch_tridiag_s<df>(a, b, length, R, ld, m, q, coef, status, st);
+    return launch_tridiag_s<double>(a, b, length, R, ld, m, q, coef, status, st);
 }
 
 mbd_status launch_energy_reduce(const double *q, int R, int dim, double omega_sum, double *scal, cudaStream_t st) {

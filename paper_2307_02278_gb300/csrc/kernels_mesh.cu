@@ -13,6 +13,61 @@ namespace {
 
 constexpr int kWarps = 8;          // warps per block in the field kernel
 
+// Vector loads/stores of VEC consecutive values (VEC in {1, 2, 4}).
+template <class T, int VEC> struct VecT;
+template <> struct VecT<float, 1> { using type = float; };
+template <> struct VecT<float, 2> { using type = float2; };
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<double, 1> { using type = double; };
+template <> struct VecT<double, 2> { using type = double2; };
+
+template <class T, int VEC> __device__ __forceinline__ void vload(const T *p, T *v) {
+    if constexpr (VEC == 4 && sizeof(T) == 8) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+        return;
+    } else {
+    using V = typename VecT<T, VEC>::type;
+    const V x = *reinterpret_cast<const V *>(p);
+    if constexpr (VEC == 1) {
+        v[0] = x;
+    } else if constexpr (VEC == 2) {
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    }
+    }
+}
+template <class T, int VEC> __device__ __forceinline__ void vstore(T *p, const T *v) {
+    if constexpr (VEC == 4 && sizeof(T) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+        return;
+    } else {
+    using V = typename VecT<T, VEC>::type;
+    V x;
+    if constexpr (VEC == 1) {
+        x = v[0];
+    } else if constexpr (VEC == 2) {
+        x.x = v[0];
+        x.y = v[1];
+    } else {
+        x.x = v[0];
+        x.y = v[1];
+        x.z = v[2];
+        x.w = v[3];
+    }
+    *reinterpret_cast<V *>(p) = x;
+    }
+}
+
 // ---------------------------------------------------------------- spreading
 // The dipole array D(k) = sum_j d_j . grad W_j(k) (Eq. dipolarr) is a sparse
 // matrix W^T (one row per mesh point, one nonzero per atom whose stencil covers
@@ -115,73 +170,69 @@ __global__ void k_scan_add(int *__restrict__ out, const int *__restrict__ bsum, 
     if (i < n) out[i] += bsum[i / 4096];
 }
 
-// D = W^T d.  A warp takes U consecutive mesh points (rows); lane = probe
-// (chunk of 32 per blockIdx.y).  The rows' pointers and their records are
-// fetched with one lane-parallel load each and broadcast by shuffles; the
-// dipole loads of 4 records are issued before they are accumulated.  Rows are
-// summed in record order (fixed), so the result is deterministic.  Columns
-// R..ld-1 (padding of an odd probe count) are written as zeros.
-template <class T>
+// D = W^T d.  A warp takes one mesh point (row) at a time, two rows
+// interleaved for memory-level parallelism; lane owns VEC consecutive probes.
+// Every lane reads the row's records directly (one broadcast 16-byte load per
+// record) and the dipoles with vector loads.  Rows are summed in record order
+// (fixed), so the result is deterministic.  Probe columns R..ld-1 (padding of
+// an odd probe count) are masked to zero.
+template <class T, int VEC>
 __global__ void __launch_bounds__(256) k_spread_csr(const T *__restrict__ d, T *__restrict__ mesh, int R, int ld,
                                                     size_t npts, const int *__restrict__ row,
                                                     const SpreadRec<T> *__restrict__ rec) {
-    constexpr int U = 8;
-    constexpr int B = 4;
-    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int U = 2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = blockIdx.y * 32 + lane;
-    const bool in_ld = r < ld;
-    const bool valid = r < R;
+    const int r0 = (blockIdx.y * 32 + lane) * VEC;
+    const bool in_ld = r0 < ld;
     const size_t nw = (size_t)gridDim.x * 8;
-    for (size_t pt0 = ((size_t)blockIdx.x * 8 + warp) * U; pt0 < npts; pt0 += nw * U) {
-        int rp = 0;
-        if (lane <= U) rp = row[min(pt0 + lane, npts)];
-        const int qs = __shfl_sync(FULL, rp, 0);
-        const int qe = __shfl_sync(FULL, rp, U);
-        int cur = 0;                                   // row being accumulated (warp-uniform)
-        int next = __shfl_sync(FULL, rp, 1);           // first record of row cur + 1
-        T acc = T(0);
-        for (int q0 = qs; q0 < qe; q0 += 32) {
-            SpreadRec<T> mine;
-            mine.w0 = mine.w1 = mine.w2 = T(0);
-            mine.atom = 0;
-            if (q0 + lane < qe) mine = rec[q0 + lane];
-            const int n = min(32, qe - q0);
-            for (int t0 = 0; t0 < n; t0 += B) {
-                T x[B], y[B], z[B], w0[B], w1[B], w2[B];
+    T mask[VEC];
 #pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    const int t = min(t0 + u, n - 1);
-                    w0[u] = __shfl_sync(FULL, mine.w0, t);
-                    w1[u] = __shfl_sync(FULL, mine.w1, t);
-                    w2[u] = __shfl_sync(FULL, mine.w2, t);
-                    const int atom = __shfl_sync(FULL, mine.atom, t);
-                    x[u] = y[u] = z[u] = T(0);
-                    if (valid && t0 + u < n) {
-                        const size_t o = (size_t)(3 * atom) * ld + r;
-                        x[u] = d[o];
-                        y[u] = d[o + ld];
-                        z[u] = d[o + 2 * (size_t)ld];
-                    }
-                }
+    for (int v = 0; v < VEC; ++v) mask[v] = (r0 + v < R) ? T(1) : T(0);
+    for (size_t pt0 = (size_t)blockIdx.x * 8 + warp; pt0 < npts; pt0 += nw * U) {
+        int q[U], qe[U];
 #pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    if (t0 + u < n) {
-                        const int q = q0 + t0 + u;
-                        while (q >= next) {                // row cur is complete
-                            if (in_ld) mesh[(pt0 + cur) * ld + r] = acc;
-                            acc = T(0);
-                            ++cur;
-                            next = __shfl_sync(FULL, rp, cur + 1);
-                        }
-                        acc += w0[u] * x[u] + w1[u] * y[u] + w2[u] * z[u];
+        for (int u = 0; u < U; ++u) {
+            const size_t pt = pt0 + u * nw;
+            q[u] = pt < npts ? row[pt] : 0;
+            qe[u] = pt < npts ? row[pt + 1] : 0;
+        }
+        T acc[U][VEC];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[u][v] = T(0);
+        bool more = true;
+        while (more) {
+            more = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (q[u] < qe[u]) {
+                    const SpreadRec<T> w = rec[q[u]];
+                    ++q[u];
+                    more = more || q[u] < qe[u];
+                    if (in_ld) {
+                        T x[VEC], y[VEC], z[VEC];
+                        const T *dj = d + (size_t)(3 * w.atom) * ld + r0;
+                        vload<T, VEC>(dj, x);
+                        vload<T, VEC>(dj + ld, y);
+                        vload<T, VEC>(dj + 2 * (size_t)ld, z);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) acc[u][v] += w.w0 * x[v] + w.w1 * y[v] + w.w2 * z[v];
                     }
                 }
             }
         }
-        for (; cur < U; ++cur) {
-            if (in_ld && pt0 + cur < npts) mesh[(pt0 + cur) * ld + r] = acc;
-            acc = T(0);
+        if (in_ld) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const size_t pt = pt0 + u * nw;
+                if (pt < npts) {
+                    T o[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) o[v] = acc[u][v] * mask[v];
+                    vstore<T, VEC>(mesh + pt * ld + r0, o);
+                }
+            }
         }
     }
 }
@@ -484,6 +535,77 @@ bool launch_ct(const FFTArgs<T> &a, unsigned grid, cudaStream_t st) {
     return true;
 }
 
+// Spreading fused with the forward FFT along k3: a block owns one (k1, k2)
+// pencil of K3 mesh points and W complex probe-pair columns.  Warp w spreads
+// rows k3 = w, w + 8, ... straight into the shared-memory tile (same records
+// and order as k_spread_csr), then the block transforms the tile along k3 and
+// writes it once.  Probe columns >= R are masked to zero.
+template <class T, int K, int W, int... RS>
+__global__ void __launch_bounds__(256) k_spread_fft3(const T *__restrict__ d, typename Cplx<T>::type *__restrict__ mesh,
+                                                     int R, int ld, int K2, const int *__restrict__ row,
+                                                     const SpreadRec<T> *__restrict__ rec,
+                                                     const typename Cplx<T>::type *__restrict__ twg) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_sf[];
+    C *buf0 = reinterpret_cast<C *>(smem_sf);
+    C *buf1 = buf0 + K * W;
+    C *tw = buf1 + K * W;
+    for (int i = threadIdx.x; i < K; i += 256) tw[i] = twg[i];
+    const int V = ld / 2;
+    const int ncb = (V + W - 1) / W;
+    const size_t pencil = blockIdx.x / ncb;              // k1 * K2 + k2
+    const int c0 = (int)(blockIdx.x % ncb) * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = c0 + lane;                           // complex column = probes 2 col, 2 col + 1
+    const bool on = lane < W && col < V;
+    const T m0 = (2 * col < R) ? T(1) : T(0), m1 = (2 * col + 1 < R) ? T(1) : T(0);
+    for (int k3 = warp; k3 < K; k3 += 8) {
+        const size_t pt = pencil * K + k3;
+        const int q0 = row[pt], q1 = row[pt + 1];
+        T ax = T(0), ay = T(0);
+        for (int q = q0; q < q1; ++q) {
+            const SpreadRec<T> w = rec[q];
+            if (on) {
+                T x[2], y[2], z[2];
+                const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
+                vload<T, 2>(dj, x);
+                vload<T, 2>(dj + ld, y);
+                vload<T, 2>(dj + 2 * (size_t)ld, z);
+                ax += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
+                ay += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+            }
+        }
+        if (lane < W) buf0[k3 * W + lane] = on ? C{ax * m0, ay * m1} : C{T(0), T(0)};
+    }
+    __syncthreads();
+    C *res = ct_stages<T, C, K, W, 1, RS...>(buf0, buf1, tw, -1);
+    const int wc = min(W, V - c0);
+    C *base = mesh + pencil * (size_t)K * V + c0;
+#pragma unroll
+    for (int it = 0; it < (K * W + 255) / 256; ++it) {
+        const int idx = it * 256 + (int)threadIdx.x;
+        if ((K * W) % 256 == 0 || idx < K * W) {
+            const int r = idx / W, c = idx % W;
+            if (c < wc) base[(size_t)r * V + c] = res[idx];
+        }
+    }
+}
+
+template <class T, int K, int W, int... RS>
+bool launch_sf3(const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row, const SpreadRec<T> *rec,
+                const typename Cplx<T>::type *tw, cudaStream_t st) {
+    using C = typename Cplx<T>::type;
+    const size_t smem = sizeof(C) * (2 * (size_t)K * W + K);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_spread_fft3<T, K, W, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return false;
+    const int V = ld / 2;
+    const unsigned grid = (unsigned)((size_t)K1 * K2 * ((V + W - 1) / W));
+    k_spread_fft3<T, K, W, RS...><<<grid, 256, smem, st>>>(d, reinterpret_cast<C *>(mesh), R, ld, K2, row, rec, tw);
+    return true;
+}
+
 // Launch the specialised pass when K has one; returns false otherwise.
 template <class T, bool FUSED>
 bool launch_fft_ct(const FFTArgs<T> &a, unsigned grid, cudaStream_t st) {
@@ -513,61 +635,6 @@ template <class T> struct FieldArgs {
     FieldOut<T> o;
 };
 
-// Vector loads/stores of VEC consecutive values (VEC in {1, 2, 4}).
-template <class T, int VEC> struct VecT;
-template <> struct VecT<float, 1> { using type = float; };
-template <> struct VecT<float, 2> { using type = float2; };
-template <> struct VecT<float, 4> { using type = float4; };
-template <> struct VecT<double, 1> { using type = double; };
-template <> struct VecT<double, 2> { using type = double2; };
-
-template <class T, int VEC> __device__ __forceinline__ void vload(const T *p, T *v) {
-    if constexpr (VEC == 4 && sizeof(T) == 8) {
-        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-        v[0] = a.x;
-        v[1] = a.y;
-        v[2] = b.x;
-        v[3] = b.y;
-        return;
-    } else {
-    using V = typename VecT<T, VEC>::type;
-    const V x = *reinterpret_cast<const V *>(p);
-    if constexpr (VEC == 1) {
-        v[0] = x;
-    } else if constexpr (VEC == 2) {
-        v[0] = x.x;
-        v[1] = x.y;
-    } else {
-        v[0] = x.x;
-        v[1] = x.y;
-        v[2] = x.z;
-        v[3] = x.w;
-    }
-    }
-}
-template <class T, int VEC> __device__ __forceinline__ void vstore(T *p, const T *v) {
-    if constexpr (VEC == 4 && sizeof(T) == 8) {
-        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
-        return;
-    } else {
-    using V = typename VecT<T, VEC>::type;
-    V x;
-    if constexpr (VEC == 1) {
-        x = v[0];
-    } else if constexpr (VEC == 2) {
-        x.x = v[0];
-        x.y = v[1];
-    } else {
-        x.x = v[0];
-        x.y = v[1];
-        x.z = v[2];
-        x.w = v[3];
-    }
-    *reinterpret_cast<V *>(p) = x;
-    }
-}
-
 // Field kernel: one block works on `apb` atoms in turn; for each atom its 8
 // warps split the work (warp w takes stencil planes t1 = w, w + 8, ... and
 // neighbours nb0 + w, nb0 + w + 8, ...; warp 0 adds the self term), lanes own
@@ -577,7 +644,8 @@ template <class T, int VEC> __device__ __forceinline__ void vstore(T *p, const T
 // fld_ewald1), l_k = Omega y_k + Diag(g) E*_k and a_k = y_k^T l_k (Eqs. lk3,
 // recurs2).  PC = spline order (0: runtime).
 template <class T, int VEC, int PC>
-__global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a, int apb) {
+__global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC > 0) ? 3 : 2)
+    k_field(FieldArgs<T> a, int apb) {
     constexpr int NLOC = 32 * VEC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rbase = blockIdx.y * NLOC;
@@ -586,9 +654,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a, int apb) 
     const int p = PC > 0 ? PC : a.g.p;
     __shared__ T red[kWarps][3][NLOC];
     __shared__ double bsum[NLOC];
-    const int tt = threadIdx.x;                 // epilogue probe (tt < NLOC)
-    const int rr = rbase + tt;
-    double part = 0.0;
+    __shared__ double pcarry[3 * NLOC > kWarps * 32 ? 3 * NLOC - kWarps * 32 : 1];
+    __shared__ double pall[3 * NLOC];
+    for (int k = threadIdx.x; k < (3 * NLOC > kWarps * 32 ? 3 * NLOC - kWarps * 32 : 1); k += blockDim.x)
+        pcarry[k] = 0.0;
+    double part = 0.0;                          // y.l of the (component, probe) this thread owns
     for (int ai = 0; ai < apb; ++ai) {
         const int idx = blockIdx.x * apb + ai;
         if (idx >= a.g.N) break;
@@ -699,39 +769,42 @@ __global__ void __launch_bounds__(kWarps * 32) k_field(FieldArgs<T> a, int apb) 
             red[warp][2][lane * VEC + v] = E2[v];
         }
         __syncthreads();
-        if (tt < NLOC && rr < a.ld) {
-            double E[3];
-            for (int c = 0; c < 3; ++c) {
-                T s = T(0);
+        // epilogue: one thread per (component, probe) so that the FP64 work
+        // spreads over 6 warps
+        for (int cp = threadIdx.x; cp < 3 * NLOC; cp += blockDim.x) {
+            const int c = cp / NLOC, t = cp - c * NLOC;
+            const int r = rbase + t;
+            if (r < a.ld) {
+                T sum = T(0);
 #pragma unroll
-                for (int w = 0; w < kWarps; ++w) s += red[w][c][tt];
-                E[c] = double(s);
-            }
-            const size_t o0 = (size_t)(3 * i) * a.ld + rr;
-            if (a.o.mode == kFieldOut) {
-                for (int c = 0; c < 3; ++c) a.o.out[o0 + (size_t)c * a.ld] = E[c];
-            } else if (a.o.mode == kFieldApply) {
-                const double w2 = a.w2[i], gi = a.g_at[i];
-                for (int c = 0; c < 3; ++c)
-                    a.o.out[o0 + (size_t)c * a.ld] = w2 * a.o.xin[o0 + (size_t)c * a.ld] + gi * E[c];
-            } else {
-                const double invb = a.o.lz.invb[rr];
-                const double w2 = a.w2[i], gi = a.g_at[i];
-                double *Yk = a.o.lz.Y + (size_t)a.o.k * (size_t)(3 * a.g.N) * a.ld;
-                for (int c = 0; c < 3; ++c) {
-                    const double y = Yk[o0 + (size_t)c * a.ld] * invb;
-                    const double l = w2 * y + gi * E[c] * invb;
-                    Yk[o0 + (size_t)c * a.ld] = y;
-                    a.o.lz.L[o0 + (size_t)c * a.ld] = l;
-                    part += y * l;
+                for (int w = 0; w < kWarps; ++w) sum += red[w][c][t];
+                const double E = double(sum);
+                const size_t o = (size_t)(3 * i + c) * a.ld + r;
+                if (a.o.mode == kFieldOut) {
+                    a.o.out[o] = E;
+                } else if (a.o.mode == kFieldApply) {
+                    a.o.out[o] = a.w2[i] * a.o.xin[o] + a.g_at[i] * E;
+                } else {
+                    const double invb = a.o.lz.invb[r];
+                    double *Yk = a.o.lz.Y + (size_t)a.o.k * (size_t)(3 * a.g.N) * a.ld;
+                    const double y = Yk[o] * invb;
+                    const double l = a.w2[i] * y + a.g_at[i] * E * invb;
+                    Yk[o] = y;
+                    a.o.lz.L[o] = l;
+                    if (cp < (int)blockDim.x) part += y * l;
+                    else pcarry[cp - blockDim.x] += y * l;   // thread cp - blockDim.x owns this slot
                 }
             }
         }
         __syncthreads();
     }
     if (a.o.mode != kFieldLanczos) return;
-    // a_k = y_k^T l_k: deterministic reduction over blocks
-    if (tt < NLOC) bsum[tt] = part;
+    // a_k = y_k^T l_k: per probe, the three components in order, then a
+    // deterministic reduction over blocks
+    for (int cp = threadIdx.x; cp < 3 * NLOC; cp += blockDim.x)
+        pall[cp] = (cp < (int)blockDim.x) ? part : pcarry[cp - blockDim.x];
+    __syncthreads();
+    for (int t = threadIdx.x; t < NLOC; t += blockDim.x) bsum[t] = pall[t] + pall[NLOC + t] + pall[2 * NLOC + t];
     __syncthreads();
     __shared__ double tot[NLOC];
     if (grid_reduce(bsum, NLOC, rbase, a.R, a.ld, a.o.lz, tot)) {
@@ -798,15 +871,48 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s) {
 template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, int R, int ld) {
     PrecData<T> &P = prec<T>(s);
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
-    const unsigned gx = (unsigned)std::min<size_t>((npts + 63) / 64, 152 * 16);
-    dim3 grid(gx, (ld + 31) / 32);
-    k_spread_csr<T><<<grid, 256, 0, s->stream>>>(d, mesh, R, ld, npts, P.srow.template as<int>(),
-                                                 P.srec.template as<SpreadRec<T>>());
+    const int vec = (sizeof(T) == 4 && ld % 4 == 0 && ld >= 128) ? 4 : ((ld % 2 == 0 && ld >= 64) ? 2 : 1);
+    const unsigned gx = (unsigned)std::min<size_t>((npts + 15) / 16, 152 * 16);
+    dim3 grid(gx, (ld + 32 * vec - 1) / (32 * vec));
+    const int *rowp = P.srow.template as<int>();
+    const SpreadRec<T> *recp = P.srec.template as<SpreadRec<T>>();
+    if (vec == 4) {
+        if constexpr (sizeof(T) == 4) k_spread_csr<T, 4><<<grid, 256, 0, s->stream>>>(d, mesh, R, ld, npts, rowp, recp);
+    } else if (vec == 2) {
+        k_spread_csr<T, 2><<<grid, 256, 0, s->stream>>>(d, mesh, R, ld, npts, rowp, recp);
+    } else {
+        k_spread_csr<T, 1><<<grid, 256, 0, s->stream>>>(d, mesh, R, ld, npts, rowp, recp);
+    }
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }
 
-template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld) {
+// Spreading fused with the first forward FFT pass when the k3 size has a
+// specialised pass and the probe-pair columns fill whole tiles; returns
+// MBD_ERR_UNSUPPORTED (nothing launched) otherwise.
+template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *mesh, int R, int ld) {
+    PrecData<T> &P = prec<T>(s);
+    constexpr int W = sizeof(T) == 4 ? 32 : 16;
+    const int V = ld / 2;
+    if (V % W != 0) return MBD_ERR_UNSUPPORTED;
+    using C = typename Cplx<T>::type;
+    const int *row = P.srow.template as<int>();
+    const SpreadRec<T> *rec = P.srec.template as<SpreadRec<T>>();
+    const C *tw = P.tw3.template as<C>();
+    bool ok = false;
+    switch (s->K[2]) {
+        case 32: ok = launch_sf3<T, 32, W, 8, 4>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
+        case 64: ok = launch_sf3<T, 64, W, 8, 8>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
+        case 96: ok = launch_sf3<T, 96, W, 8, 4, 3>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
+        case 128: ok = launch_sf3<T, 128, W, 8, 8, 2>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
+        default: ok = false;
+    }
+    if (!ok) return MBD_ERR_UNSUPPORTED;
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bool skip_first) {
     using C = typename Cplx<T>::type;
     PrecData<T> &P = prec<T>(s);
     const int V = ld / 2;
@@ -845,7 +951,7 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld) {
         MBD_LAUNCH_CHECK();
         return MBD_OK;
     };
-    MBD_TRY(run(2, K1 * K2, V, -1, false));            // forward along k3
+    if (!skip_first) MBD_TRY(run(2, K1 * K2, V, -1, false));   // forward along k3
     MBD_TRY(run(1, K1, K3 * V, -1, false));            // forward along k2
     MBD_TRY(run(0, 1, K2 * K3 * V, -1, true));         // forward k1, x G, inverse k1
     MBD_TRY(run(1, K1, K3 * V, +1, false));            // inverse along k2
@@ -898,8 +1004,10 @@ template mbd_status build_spread_matrix<double>(mbd_system *);
 template mbd_status build_spread_matrix<float>(mbd_system *);
 template mbd_status launch_spread<double>(mbd_system *, const double *, double *, int, int);
 template mbd_status launch_spread<float>(mbd_system *, const float *, float *, int, int);
-template mbd_status launch_convolve<double>(mbd_system *, double *, int);
-template mbd_status launch_convolve<float>(mbd_system *, float *, int);
+template mbd_status launch_convolve<double>(mbd_system *, double *, int, bool);
+template mbd_status launch_convolve<float>(mbd_system *, float *, int, bool);
+template mbd_status launch_spread_fft3<double>(mbd_system *, const double *, double *, int, int);
+template mbd_status launch_spread_fft3<float>(mbd_system *, const float *, float *, int, int);
 template mbd_status launch_field<double>(mbd_system *, const double *, const double *, int, int,
                                          const FieldOut<double> &);
 template mbd_status launch_field<float>(mbd_system *, const float *, const float *, int, int,

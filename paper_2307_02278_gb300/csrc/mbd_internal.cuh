@@ -210,6 +210,7 @@ struct mbd_system {
     int K[3], p;
     double ewald_beta, r_cut, damp_cut, damp_beta, damp_d;
     int precision;
+    int eigen_df64;     // tridiagonal eigensolve in double-float instead of FP64
     cudaStream_t stream;
     double omega_sum;
     mbd::FFTDim fft[3];
@@ -248,7 +249,9 @@ template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod
 // mesh stages
 template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, int R, int ld);
 template <class T> mbd_status build_spread_matrix(mbd_system *s);
-template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld);   // in place
+// in place; skip_first: the forward k3 pass was already done (launch_spread_fft3)
+template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bool skip_first = false);
+template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *mesh, int R, int ld);
 enum FieldMode { kFieldOut = 0, kFieldApply = 1, kFieldLanczos = 2 };
 template <class T> struct FieldOut {
     int mode;
@@ -266,7 +269,7 @@ mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int 
                              int rows, const double *g, void *dout, int dtype_bytes, int nblk);
 // q [R] and, when coef != nullptr, c = Delta^{-1/2} e_1 as coef [m][ld]
 mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
-                          double *coef, int *status, cudaStream_t st);
+                          double *coef, int *status, cudaStream_t st, bool df64 = false);
 mbd_status launch_energy_reduce(const double *q, int R, int dim, double omega_sum, double *scal, cudaStream_t st);
 mbd_status launch_probes(uint64_t seed, int first, int R, int dim, double *v, cudaStream_t st);
 mbd_status launch_dense_step(const double *c, int dim, const LanczosView &lz, int k, int R, int ld, int nblk,

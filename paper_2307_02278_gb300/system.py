@@ -12,9 +12,11 @@ from ctypes import byref, c_double, c_void_p
 import numpy as np
 import torch
 
-from ._abi import (MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES, Info, Profile, SystemDesc, check, lib)
+from ._abi import (MBD_EIGEN_DF64, MBD_EIGEN_FP64, MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES, Info, Profile,
+                   SystemDesc, check, lib)
 
 PRECISIONS = {"fp64": MBD_FP64, "mixed": MBD_MIXED}
+EIGEN = {"fp64": MBD_EIGEN_FP64, "df64": MBD_EIGEN_DF64}
 
 
 def _dptr(a: np.ndarray):
@@ -31,7 +33,8 @@ class MBDSystem:
     """One periodic system on the GPU (mbd_create_system)."""
 
     def __init__(self, cell, pos, alpha, omega, r_vdw, *, damp_beta=0.83, damp_d=6.0, ewald_beta=0.35,
-                 r_cut=10.0, damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64", stream=None):
+                 r_cut=10.0, damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64",
+                 eigen_precision="fp64", stream=None):
         self._handle = None
         self.n_atoms = int(np.asarray(pos).shape[0])
         self._pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
@@ -50,6 +53,7 @@ class MBDSystem:
         d.mesh[:] = [int(k) for k in mesh]
         d.spline_order = int(spline_order)
         d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d.eigen_precision = EIGEN[eigen_precision] if isinstance(eigen_precision, str) else int(eigen_precision)
         self.precision = precision
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream()

@@ -270,3 +270,39 @@ def test_lanczos_probe_widths(mbd, R):
     e, det = mbd.MBDSystem.from_workload(s).lanczos_energy(R, 8, 1234, details=True)
     q_ref, _, _, _ = slq(Operator(s, "spme"), 3 * s.n_atoms, R, 8, 1234)
     np.testing.assert_allclose(det["q"], q_ref, rtol=1e-8)
+
+
+@pytest.mark.parametrize("mesh", [(16, 20, 32), (12, 16, 64)])
+@pytest.mark.parametrize("R", [32, 64, 128])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_spread_fft_path(mbd, mesh, R, precision):
+    """Meshes whose k3 size has the fused spreading + first FFT pass (whole
+    probe-pair tiles): Lanczos quadratures and forces against the oracle."""
+    s = _small(mesh=mesh)
+    g = mbd.MBDSystem.from_workload(s, precision=precision)
+    e, det = g.lanczos_energy(R, 6, 4321, details=True)
+    op = Operator(s, "spme")
+    q_ref, _, _, _ = slq(op, 3 * s.n_atoms, R, 6, 4321)
+    np.testing.assert_allclose(det["q"], q_ref, rtol=1e-8 if precision == "fp64" else 2e-6)
+    if R == 32:
+        e2, f = g.energy_forces(R, 6, 4321)
+        f_ref, _, _ = estimator_forces(op, R, 6, 4321)
+        tol = 1e-8 if precision == "fp64" else 1e-4
+        assert np.abs(f.cpu().numpy() - f_ref).max() <= tol * np.abs(f_ref).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_df64_eigensolver_option(mbd, precision):
+    """MBD_EIGEN_DF64 changes only the tridiagonal eigensolve: identical Lanczos
+    coefficients, quadratures within 1e-12 and forces within 1e-11 of FP64."""
+    s = _small()
+    g64 = mbd.MBDSystem.from_workload(s, precision=precision)
+    gdf = mbd.MBDSystem.from_workload(s, precision=precision, eigen_precision="df64")
+    e1, d1 = g64.lanczos_energy(16, 30, 5, details=True)
+    e2, d2 = gdf.lanczos_energy(16, 30, 5, details=True)
+    np.testing.assert_array_equal(d2["a"], d1["a"])
+    np.testing.assert_allclose(d2["q"], d1["q"], rtol=1e-12)
+    _, f1 = g64.energy_forces(8, 20, 5)
+    _, f2 = gdf.energy_forces(8, 20, 5)
+    f1, f2 = f1.cpu().numpy(), f2.cpu().numpy()
+    assert np.abs(f2 - f1).max() <= 1e-11 * np.abs(f1).max()
