@@ -159,6 +159,31 @@ mbd_status mbd_convolve(mbd_system *sys, int32_t nvec, const double *mesh_in_dev
 mbd_status mbd_tridiag_quadrature(int32_t n_probes, int32_t n_steps, const double *a_host,
                                   const double *b_host, double *q_host);
 
+/* The quadrature of mbd_tridiag_quadrature for callers that cannot let the
+ * library allocate device memory: callers whose device memory belongs to
+ * another allocator (a framework's caching allocator, a pool registered with a
+ * communication library) or that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree imply.  The paper has no
+ * counterpart; this is a library convenience.
+ *   a_dev, b_dev  device FP64 [R][m], caller-owned, same meaning as the host
+ *                 arrays of mbd_tridiag_quadrature (b[l][k] couples k and k+1;
+ *                 from the first zero on, entries are ignored)
+ *   q_dev         device FP64 [R] output, caller-owned
+ *   cuda_stream   cudaStream_t for the work, or NULL for the legacy default stream
+ * The call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  Its scratch (about 2.1 MB) is one file-scope device array that every
+ * GPU loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and caches
+ * it; make that first call before any stream capture.  Every call shares the
+ * one array (it keeps the last call's contents; the call clears what must
+ * start at zero), so calls that overlap on the GPU, for example on two streams,
+ * race: serialise them.  Returns MBD_ERR_INVALID_ARG for R > MBD_NOALLOC_MAX_PROBES
+ * or m > 128, MBD_ERR_NOT_POSITIVE_DEFINITE if a Ritz value is <= 0.  The call
+ * returns after its work has finished. */
+#define MBD_NOALLOC_MAX_PROBES 1024
+mbd_status mbd_tridiag_quadrature_noalloc(int32_t n_probes, int32_t n_steps, const double *a_dev,
+                                          const double *b_dev, double *q_dev, void *cuda_stream);
+
 /* The Lanczos layer alone: the same recurrence, quadrature and estimator as
  * mbd_lanczos_energy, driven by a dense symmetric FP64 matrix C_dev [dim][dim]
  * (device).  energy = (1/2) trace - 1.5 * omega_sum. */

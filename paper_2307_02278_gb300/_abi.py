@@ -88,6 +88,7 @@ SIGNATURES = {
     "mbd_spread": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_convolve": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_tridiag_quadrature": (c_int, [c_int32, c_int32, PD, PD, PD]),
+    "mbd_tridiag_quadrature_noalloc": (c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "mbd_lanczos_energy_dense": (c_int, [c_int32, c_void_p, c_double, c_int32, c_int32, c_uint64, PD, PD, PD]),
     "mbd_get_info": (c_int, [c_void_p, POINTER(Info)]),
     "mbd_profile_enable": (c_int, [c_void_p, c_int32]),
