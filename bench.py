@@ -251,9 +251,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2307_02278_gb300.parallel import reduce_estimates, shard_seed
     s = config(WORKLOAD)
     R, m = s.n_probes, s.n_steps
-    seed = (s.probe_seed + ((rank * R) << 32)) % (1 << 64)
+    seed = shard_seed(s.probe_seed, rank, R)
     stream = torch.cuda.Stream()
     sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, eigen_precision=args.eigen, stream=stream)
     info = sysm.info()
@@ -266,10 +267,7 @@ def run_ours(args, world, rank, local):
         if world > 1:
             with torch.cuda.stream(stream):
                 energy_t.fill_(e)
-                dist.all_reduce(energy_t)
-                dist.all_reduce(forces)
-                energy_t.div_(world)
-                forces.div_(world)
+                reduce_estimates(energy_t, forces)
         return e
 
     for _ in range(args.warmup):

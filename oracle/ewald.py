@@ -98,6 +98,27 @@ def pair_list(cell: np.ndarray, pos: np.ndarray, rmax: float, chunk: int = 256):
     return np.concatenate(out_i), np.concatenate(out_j), np.concatenate(out_r)
 
 
+def pair_list_tree(cell: np.ndarray, pos: np.ndarray, rmax: float):
+    """The same pair set as pair_list for an orthorhombic cell whose shortest
+    edge exceeds 2 rmax (each pair then has one image within rmax, the minimum
+    image), found with a periodic k-d tree; falls back to pair_list otherwise."""
+    cell = np.asarray(cell, dtype=np.float64)
+    box = np.diag(cell)
+    if np.any(np.abs(cell - np.diag(box)) > 0) or rmax >= 0.5 * box.min():
+        return pair_list(cell, pos, rmax)
+    from scipy.spatial import cKDTree
+    pos = wrap_positions(cell, pos)
+    tree = cKDTree(pos, boxsize=box)
+    pairs = tree.query_pairs(rmax, output_type="ndarray")
+    i = np.concatenate([pairs[:, 0], pairs[:, 1]])
+    j = np.concatenate([pairs[:, 1], pairs[:, 0]])
+    r = pos[i] - pos[j]
+    r -= box * np.round(r / box)
+    keep = np.einsum("ij,ij->i", r, r) < rmax * rmax
+    order = np.lexsort((j[keep], i[keep]))
+    return i[keep][order], j[keep][order], r[keep][order]
+
+
 def real_space_tensor(sys, i, j, rvec, r_cut: float, damp_cut: float) -> np.ndarray:
     """Pair tensor of E^dir including the damping correction of Eq. fld_ewald:
     A(r) = [|r|<r_cut] (B1 I - B2 r r^T) - [|r|<damp_cut] (1 - s(|r|)) T(r)."""

@@ -8,21 +8,24 @@ from __future__ import annotations
 
 import numpy as np
 
-from .ewald import apply_T, cutoffs, pair_list, real_space_matrix
+from .ewald import apply_T, cutoffs, pair_list, pair_list_tree, real_space_matrix
 from .model import g_vector, omega_diag
 
 
 class Operator:
     """C for one system and one evaluation mode ("exact", "same_split", "spme")."""
 
-    def __init__(self, sys, mode: str = "spme"):
+    def __init__(self, sys, mode: str = "spme", tree_pairs: bool | None = None):
         self.sys = sys
         self.mode = mode
         self.n = sys.pos.shape[0]
         self.g = g_vector(sys.alpha, sys.omega)
         self.w2 = omega_diag(sys.omega)
         real_mode = "exact" if mode == "exact" else "same_split"
-        self.pairs = pair_list(sys.cell, sys.pos, max(cutoffs(sys, real_mode)))
+        rmax = max(cutoffs(sys, real_mode))
+        if tree_pairs is None:
+            tree_pairs = self.n > 2000
+        self.pairs = (pair_list_tree if tree_pairs else pair_list)(sys.cell, sys.pos, rmax)
         self.real = real_space_matrix(sys, real_mode, self.pairs)
 
     def field(self, d: np.ndarray) -> np.ndarray:

@@ -567,8 +567,7 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
     fo.xin = nullptr;
     fo.lz = z.v;
     // the fused spread + k3 pass exists for the specialised sizes with whole probe-pair tiles
-    const bool fuse3 = (s->K[2] == 32 || s->K[2] == 64 || s->K[2] == 96 || s->K[2] == 128) &&
-                       ((z.ld / 2) % (sizeof(T) == 4 ? 32 : 16) == 0) && s->K[0] * s->K[1] > 0;
+    const bool fuse3 = spread_fft3_supported(s->K[2], z.ld, (int)sizeof(T));
     for (int k = 0; k < m; ++k) {
         MBD_STAGE(s, MBD_STAGE_PROLOGUE, 1,
                   launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
@@ -659,8 +658,7 @@ mbd_status forces_impl(mbd_system *s, int R, int m, uint64_t seed, double *energ
     MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
               launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m,
                                         P.d.template as<T>(), ld2));
-    const bool fuse3 = (s->K[2] == 32 || s->K[2] == 64 || s->K[2] == 96 || s->K[2] == 128) &&
-                       ((ld2 / 2) % (sizeof(T) == 4 ? 32 : 16) == 0);
+    const bool fuse3 = spread_fft3_supported(s->K[2], ld2, (int)sizeof(T));
     if (fuse3) {
         MBD_STAGE(s, MBD_STAGE_FORCE_SPREAD, 1,
                   launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));

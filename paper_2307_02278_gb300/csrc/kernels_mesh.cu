@@ -616,6 +616,7 @@ bool launch_fft_ct(const FFTArgs<T> &a, unsigned grid, cudaStream_t st) {
         case 64: return launch_ct<T, FUSED, 64, W, 8, 8>(a, grid, st);
         case 96: return launch_ct<T, FUSED, 96, W, 8, 4, 3>(a, grid, st);
         case 128: return launch_ct<T, FUSED, 128, W, 8, 8, 2>(a, grid, st);
+        case 192: return launch_ct<T, FUSED, 192, W, 8, 8, 3>(a, grid, st);
         default: return false;
     }
 }
@@ -890,6 +891,12 @@ template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, 
 // Spreading fused with the first forward FFT pass when the k3 size has a
 // specialised pass and the probe-pair columns fill whole tiles; returns
 // MBD_ERR_UNSUPPORTED (nothing launched) otherwise.
+bool spread_fft3_supported(int K3, int ld, int real_bytes) {
+    const int W = real_bytes == 4 ? 32 : 16;
+    const bool k_ok = K3 == 32 || K3 == 64 || K3 == 96 || K3 == 128 || K3 == 192;
+    return k_ok && (ld / 2) % W == 0;
+}
+
 template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *mesh, int R, int ld) {
     PrecData<T> &P = prec<T>(s);
     constexpr int W = sizeof(T) == 4 ? 32 : 16;
@@ -905,6 +912,7 @@ template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *m
         case 64: ok = launch_sf3<T, 64, W, 8, 8>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
         case 96: ok = launch_sf3<T, 96, W, 8, 4, 3>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
         case 128: ok = launch_sf3<T, 128, W, 8, 8, 2>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
+        case 192: ok = launch_sf3<T, 192, W, 8, 8, 3>(d, mesh, R, ld, s->K[0], s->K[1], row, rec, tw, s->stream); break;
         default: ok = false;
     }
     if (!ok) return MBD_ERR_UNSUPPORTED;

@@ -252,6 +252,7 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s);
 // in place; skip_first: the forward k3 pass was already done (launch_spread_fft3)
 template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bool skip_first = false);
 template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *mesh, int R, int ld);
+bool spread_fft3_supported(int K3, int ld, int real_bytes);
 enum FieldMode { kFieldOut = 0, kFieldApply = 1, kFieldLanczos = 2 };
 template <class T> struct FieldOut {
     int mode;

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle.ewald import (apply_T, pair_list, real_space_tensor, real_space_tensor_grad,
+from oracle.ewald import (apply_T, pair_list, pair_list_tree, real_space_tensor, real_space_tensor_grad,
                           reciprocal_field_direct)
 from oracle.model import cell_volume
 from oracle.operator import Operator
@@ -110,3 +110,14 @@ def test_real_space_tensor_grad_fd():
         e[c] = h
         fd = (real_space_tensor(s, i, j, r + e, 5.4, 5.8) - real_space_tensor(s, i, j, r - e, 5.4, 5.8)) / (2 * h)
         np.testing.assert_allclose(g[inside, ..., c], fd[inside], rtol=1e-5, atol=1e-10)
+
+
+@pytest.mark.parametrize("n,box,rmax", [(40, 22.0, 10.0), (300, 30.0, 7.0)])
+def test_pair_list_tree_matches_brute_force(n, box, rmax):
+    """The k-d tree pair search returns exactly the brute-force pair set."""
+    s = random_system(n, box, 91 + n, mesh=(24, 24, 24))
+    i, j, r = pair_list(s.cell, s.pos, rmax)
+    i2, j2, r2 = pair_list_tree(s.cell, s.pos, rmax)
+    a = sorted(zip(i.tolist(), j.tolist(), np.round(r, 9).tolist()))
+    b = sorted(zip(i2.tolist(), j2.tolist(), np.round(r2, 9).tolist()))
+    assert a == b
