@@ -430,9 +430,10 @@ __global__ void __launch_bounds__(256) k_fft_pass(FFTArgs<T> a) {
 // Compile-time specialisation of the pass for common mesh sizes: K, the
 // radix list, the tile width W and every stride are constants, so the index
 // arithmetic folds away and each stage is one unrolled butterfly per thread.
-template <class T, class C, int R, int K, int W, int NS>
-__device__ __forceinline__ void ct_stage(const C *__restrict__ in, C *__restrict__ out, const C *__restrict__ tw,
-                                         int sign) {
+template <class T, class C, int R, int K, int W, int NS, bool IN_G, bool OUT_G, bool MULG>
+__device__ __forceinline__ void ct_stage(const C *__restrict__ in_s, const C *__restrict__ in_g, C *__restrict__ out_s,
+                                         C *__restrict__ out_g, size_t gs, int wc, const C *__restrict__ tw, int sign,
+                                         const T *__restrict__ G, size_t gstride, int c0, int V) {
     constexpr int nb = K / R;
     constexpr int step = K / (NS * R);
     constexpr int total = nb * W;
@@ -443,7 +444,12 @@ __device__ __forceinline__ void ct_stage(const C *__restrict__ in, C *__restrict
         const int j = idx / W, col = idx % W;
         C v[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = in[(j + q * nb) * W + col];
+        for (int q = 0; q < R; ++q) {
+            if (IN_G)
+                v[q] = col < wc ? in_g[(size_t)(j + q * nb) * gs + col] : C{T(0), T(0)};
+            else
+                v[q] = in_s[(j + q * nb) * W + col];
+        }
         const int jm = j % NS;
         if (NS > 1 && jm != 0) {
 #pragma unroll
@@ -456,70 +462,71 @@ __device__ __forceinline__ void ct_stage(const C *__restrict__ in, C *__restrict
         dft<T, C, R>(v, sign);
         const int base = (j / NS) * NS * R + jm;
 #pragma unroll
-        for (int q = 0; q < R; ++q) out[(base + q * NS) * W + col] = v[q];
+        for (int q = 0; q < R; ++q) {
+            const int row = base + q * NS;
+            if (MULG && col < wc) {
+                const T gv = G[(size_t)row * gstride + (c0 + col) / V];
+                v[q].x *= gv;
+                v[q].y *= gv;
+            }
+            if (OUT_G) {
+                if (col < wc) out_g[(size_t)row * gs + col] = v[q];
+            } else {
+                out_s[row * W + col] = v[q];
+            }
+        }
     }
 }
 
-template <class T, class C, int K, int W, int NS, int R, int... RS>
-__device__ __forceinline__ C *ct_stages(C *in, C *out, const C *tw, int sign) {
-    ct_stage<T, C, R, K, W, NS>(in, out, tw, sign);
-    __syncthreads();
-    if constexpr (sizeof...(RS) > 0)
-        return ct_stages<T, C, K, W, NS * R, RS...>(out, in, tw, sign);
-    else
-        return out;
+// A run of Stockham stages: the first reads the global tile (IN_G) or shared
+// buffer sin, intermediate results ping-pong between sin and sout, the last
+// writes the global tile (OUT_G) or shared memory, multiplying by G (MULG).
+// Returns the shared buffer holding the result when it stays in shared memory.
+template <class T, class C, int K, int W, int NS, bool IN_G, bool OUT_G, bool MULG, int R, int... RS>
+__device__ __forceinline__ C *ct_pipe(const C *gin, C *gout, size_t gs, int wc, C *sin, C *sout, const C *tw, int sign,
+                                      const T *G, size_t gstride, int c0, int V) {
+    constexpr bool last = sizeof...(RS) == 0;
+    ct_stage<T, C, R, K, W, NS, IN_G, last && OUT_G, last && MULG>(sin, gin, sout, gout, gs, wc, tw, sign, G, gstride,
+                                                                   c0, V);
+    if constexpr (last) {
+        return sout;
+    } else {
+        __syncthreads();
+        return ct_pipe<T, C, K, W, NS * R, false, OUT_G, MULG, RS...>(gin, gout, gs, wc, sout, sin, tw, sign, G, gstride,
+                                                                       c0, V);
+    }
 }
 
+// One pass with compile-time K, W and radices (at least two stages).  The
+// first stage loads the global tile straight into registers and the last one
+// stores straight from registers, so shared memory carries only the exchanges
+// between stages; the fused pass (forward, x G, inverse) multiplies by G in the
+// last forward stage.
 template <class T, bool FUSED, int K, int W, int... RS>
 __global__ void __launch_bounds__(256) k_fft_ct(FFTArgs<T> a) {
     using C = typename Cplx<T>::type;
+    static_assert(sizeof...(RS) >= 2, "single-stage sizes would read and write the same global tile");
     extern __shared__ __align__(16) unsigned char smem_ct[];
-    C *buf[2] = {reinterpret_cast<C *>(smem_ct), reinterpret_cast<C *>(smem_ct) + K * W};
-    C *tw = reinterpret_cast<C *>(smem_ct) + 2 * K * W;
+    C *buf0 = reinterpret_cast<C *>(smem_ct), *buf1 = buf0 + K * W;
+    C *tw = buf1 + K * W;
     for (int i = threadIdx.x; i < K; i += 256) tw[i] = a.tw[i];
+    __syncthreads();
     const int ncb = (a.inner + W - 1) / W;
     const size_t outer = blockIdx.x / ncb;
     const int c0 = (int)(blockIdx.x % ncb) * W;
     const int wc = min(W, a.inner - c0);
     C *base = a.data + outer * (size_t)K * a.inner + c0;
-#pragma unroll
-    for (int it = 0; it < (K * W + 255) / 256; ++it) {
-        const int idx = it * 256 + (int)threadIdx.x;
-        if ((K * W) % 256 == 0 || idx < K * W) {
-            const int row = idx / W, col = idx % W;
-            buf[0][idx] = col < wc ? base[(size_t)row * a.inner + col] : C{T(0), T(0)};
-        }
-    }
-    __syncthreads();
-    C *res;
+    const size_t gstride = (size_t)(a.inner / a.V);
     if (FUSED) {
-        res = ct_stages<T, C, K, W, 1, RS...>(buf[0], buf[1], tw, -1);
-        C *other = (res == buf[0]) ? buf[1] : buf[0];
-        const size_t gstride = (size_t)(a.inner / a.V);
-#pragma unroll
-        for (int it = 0; it < (K * W + 255) / 256; ++it) {
-            const int idx = it * 256 + (int)threadIdx.x;
-            if ((K * W) % 256 == 0 || idx < K * W) {
-                const int row = idx / W, col = idx % W;
-                if (col < wc) {
-                    const T gv = a.G[(size_t)row * gstride + (c0 + col) / a.V];
-                    res[idx].x *= gv;
-                    res[idx].y *= gv;
-                }
-            }
-        }
+        C *res = ct_pipe<T, C, K, W, 1, true, false, true, RS...>(base, base, a.inner, wc, buf0, buf1, tw, -1, a.G,
+                                                                   gstride, c0, a.V);
         __syncthreads();
-        res = ct_stages<T, C, K, W, 1, RS...>(res, other, tw, +1);
+        C *other = (res == buf0) ? buf1 : buf0;
+        ct_pipe<T, C, K, W, 1, false, true, false, RS...>(base, base, a.inner, wc, res, other, tw, +1, a.G, gstride, c0,
+                                                           a.V);
     } else {
-        res = ct_stages<T, C, K, W, 1, RS...>(buf[0], buf[1], tw, a.sign);
-    }
-#pragma unroll
-    for (int it = 0; it < (K * W + 255) / 256; ++it) {
-        const int idx = it * 256 + (int)threadIdx.x;
-        if ((K * W) % 256 == 0 || idx < K * W) {
-            const int row = idx / W, col = idx % W;
-            if (col < wc) base[(size_t)row * a.inner + col] = res[idx];
-        }
+        ct_pipe<T, C, K, W, 1, true, true, false, RS...>(base, base, a.inner, wc, buf0, buf1, tw, a.sign, a.G, gstride,
+                                                          c0, a.V);
     }
 }
 
@@ -559,36 +566,54 @@ __global__ void __launch_bounds__(256) k_spread_fft3(const T *__restrict__ d, ty
     const int col = c0 + lane;                           // complex column = probes 2 col, 2 col + 1
     const bool on = lane < W && col < V;
     const T m0 = (2 * col < R) ? T(1) : T(0), m1 = (2 * col + 1 < R) ? T(1) : T(0);
-    for (int k3 = warp; k3 < K; k3 += 8) {
-        const size_t pt = pencil * K + k3;
-        const int q0 = row[pt], q1 = row[pt + 1];
-        T ax = T(0), ay = T(0);
-        for (int q = q0; q < q1; ++q) {
-            const SpreadRec<T> w = rec[q];
-            if (on) {
-                T x[2], y[2], z[2];
-                const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
-                vload<T, 2>(dj, x);
-                vload<T, 2>(dj + ld, y);
-                vload<T, 2>(dj + 2 * (size_t)ld, z);
-                ax += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
-                ay += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+    // two rows (k3 and k3 + 8) per warp iteration: two independent load chains
+    for (int k3 = warp; k3 < K; k3 += 16) {
+        const int kb = k3 + 8;
+        const size_t pa = pencil * K + k3, pb = pencil * K + kb;
+        int qa = row[pa];
+        const int qa1 = row[pa + 1];
+        int qb = 0, qb1 = 0;
+        if (kb < K) {
+            qb = row[pb];
+            qb1 = row[pb + 1];
+        }
+        T ax = T(0), ay = T(0), bx = T(0), by = T(0);
+        while (qa < qa1 || qb < qb1) {
+            if (qa < qa1) {
+                const SpreadRec<T> w = rec[qa++];
+                if (on) {
+                    T x[2], y[2], z[2];
+                    const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
+                    vload<T, 2>(dj, x);
+                    vload<T, 2>(dj + ld, y);
+                    vload<T, 2>(dj + 2 * (size_t)ld, z);
+                    ax += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
+                    ay += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+                }
+            }
+            if (qb < qb1) {
+                const SpreadRec<T> w = rec[qb++];
+                if (on) {
+                    T x[2], y[2], z[2];
+                    const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
+                    vload<T, 2>(dj, x);
+                    vload<T, 2>(dj + ld, y);
+                    vload<T, 2>(dj + 2 * (size_t)ld, z);
+                    bx += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
+                    by += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+                }
             }
         }
-        if (lane < W) buf0[k3 * W + lane] = on ? C{ax * m0, ay * m1} : C{T(0), T(0)};
-    }
-    __syncthreads();
-    C *res = ct_stages<T, C, K, W, 1, RS...>(buf0, buf1, tw, -1);
-    const int wc = min(W, V - c0);
-    C *base = mesh + pencil * (size_t)K * V + c0;
-#pragma unroll
-    for (int it = 0; it < (K * W + 255) / 256; ++it) {
-        const int idx = it * 256 + (int)threadIdx.x;
-        if ((K * W) % 256 == 0 || idx < K * W) {
-            const int r = idx / W, c = idx % W;
-            if (c < wc) base[(size_t)r * V + c] = res[idx];
+        if (lane < W) {
+            buf0[k3 * W + lane] = on ? C{ax * m0, ay * m1} : C{T(0), T(0)};
+            if (kb < K) buf0[kb * W + lane] = on ? C{bx * m0, by * m1} : C{T(0), T(0)};
         }
     }
+    __syncthreads();
+    const int wc = min(W, V - c0);
+    C *base = mesh + pencil * (size_t)K * V + c0;
+    ct_pipe<T, C, K, W, 1, false, true, false, RS...>(base, base, (size_t)V, wc, buf0, buf1, tw, -1,
+                                                       (const T *)nullptr, 0, c0, V);
 }
 
 template <class T, int K, int W, int... RS>
