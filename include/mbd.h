@@ -71,6 +71,7 @@ enum { MBD_EIGEN_FP64 = 0, MBD_EIGEN_DF64 = 1 };
 enum { MBD_TERM_REAL = 1, MBD_TERM_RECIP = 2, MBD_TERM_SELF = 4, MBD_TERM_ALL = 7 };
 
 typedef struct mbd_system mbd_system;   /* opaque, owned by the library */
+typedef struct mbd_batch mbd_batch;     /* opaque: several independent systems */
 
 /* One periodic system (Eq. ham parameters, Ewald/SPME settings).
  * damping: T'_ij = s(R_ij) T_ij with the Fermi form
@@ -133,6 +134,47 @@ mbd_status mbd_lanczos_energy(mbd_system *sys, int32_t n_probes, int32_t n_steps
  * forces_dev: device FP64 [N][3].  Other arguments as mbd_lanczos_energy. */
 mbd_status mbd_energy_forces(mbd_system *sys, int32_t n_probes, int32_t n_steps, uint64_t seed,
                              double *energy, double *forces_dev);
+
+/* ---- batches of independent systems ----
+ * The probes of one system are independent of one another, and so are whole
+ * systems: the paper's parallel scheme distributes independent stochastic
+ * samples with one reduction before the trace (Sections 4 and 5).  A
+ * batch holds n_sys systems of uneven sizes (each its own cell, atoms and mesh)
+ * on one GPU.  mbd_batch_lanczos_energy runs Algorithm 1 for every member at
+ * once: the first call with a given (n_probes, n_steps) records every member's
+ * whole run (probes, m Lanczos steps, quadrature, energy) as an independent
+ * branch of one CUDA graph; later calls with the same (n_probes, n_steps)
+ * replay that graph with new seeds.  Members cannot be reached one at a time;
+ * create separate systems for that. */
+
+/* descs: host array [n_sys] of system descriptions (each as for
+ * mbd_create_system; all must share one precision).  cuda_stream: the stream
+ * the batch's work is ordered on (NULL: legacy default stream); the library
+ * captures on a stream of its own.  *out receives the handle on MBD_OK. */
+mbd_status mbd_create_batch(int32_t n_sys, const mbd_system_desc *descs, void *cuda_stream, mbd_batch **out);
+
+/* Release the batch, its members and its graph (NULL is ignored). */
+void mbd_destroy_batch(mbd_batch *batch);
+
+/* Energies of every member (Algorithm 1 per member).  seeds: host [n_sys],
+ * member i uses seeds[i] with the probe rule of mbd_lanczos_energy, so member
+ * i's energy equals mbd_lanczos_energy on the same description and seed up to
+ * summation order (the kernels and their order are the same).  energies: host
+ * [n_sys] (required); traces: host [n_sys] or NULL.  On a member's failure
+ * (MBD_ERR_NOT_POSITIVE_DEFINITE, MBD_ERR_NONFINITE) the call returns that
+ * status, writes nothing, and *failed_member (if not NULL) names the first
+ * failing member. */
+mbd_status mbd_batch_lanczos_energy(mbd_batch *batch, int32_t n_probes, int32_t n_steps, const uint64_t *seeds,
+                                    double *energies, double *traces, int32_t *failed_member);
+
+/* Number of members, the kernel nodes of the current graph (0 before the
+ * first run) and the total atoms of the batch. */
+typedef struct {
+    int32_t n_sys;
+    int64_t graph_kernels;
+    int64_t total_atoms;
+} mbd_batch_info;
+mbd_status mbd_batch_get_info(const mbd_batch *batch, mbd_batch_info *info);
 
 /* ---- stage-level entry points (per-stage checks and users of single stages) ---- */
 

@@ -66,6 +66,14 @@ class Profile(ctypes.Structure):
     ]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_sys", c_int32),
+        ("graph_kernels", c_int64),
+        ("total_atoms", c_int64),
+    ]
+
+
 class MBDError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
@@ -83,6 +91,10 @@ SIGNATURES = {
     "mbd_apply_C": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_lanczos_energy": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, PD, PD, PD]),
     "mbd_energy_forces": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, c_void_p]),
+    "mbd_create_batch": (c_int, [c_int32, POINTER(SystemDesc), c_void_p, POINTER(c_void_p)]),
+    "mbd_destroy_batch": (None, [c_void_p]),
+    "mbd_batch_lanczos_energy": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_uint64), PD, PD, POINTER(c_int32)]),
+    "mbd_batch_get_info": (c_int, [c_void_p, POINTER(BatchInfo)]),
     "mbd_generate_probes": (c_int, [c_uint64, c_int32, c_int32, c_int32, c_void_p]),
     "mbd_field": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_int32]),
     "mbd_spread": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),

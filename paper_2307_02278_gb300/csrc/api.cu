@@ -531,9 +531,6 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     MBD_TRY(s->q.ensure(sizeof(double) * ld));
     MBD_TRY(s->scal.ensure(sizeof(double) * 16));
     MBD_TRY(s->status.ensure(sizeof(int) * 4));
-    MBD_CUDA_TRY(cudaMemsetAsync(s->a.ptr, 0, sizeof(double) * (size_t)m * ld, s->stream));
-    MBD_CUDA_TRY(cudaMemsetAsync(s->b.ptr, 0, sizeof(double) * (size_t)m * ld, s->stream));
-    MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
     z.v.Y = s->Y.as<double>();
     z.v.L = s->L.as<double>();
     z.v.a = s->a.as<double>();
@@ -554,12 +551,27 @@ template <class T> mbd_status ensure_mesh(mbd_system *s, int ld) {
     return MBD_OK;
 }
 
-// Algorithm 1 with Algorithm 2 per step: m Lanczos steps for all R probes.
-template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t seed, Lz &z, bool full = false) {
+// Workspace for an m-step run with R probes (allocations only: eager).
+template <class T> mbd_status prepare_lanczos(mbd_system *s, int R, int m, Lz &z, bool full) {
     const int rows = 3 * s->N;
     MBD_TRY(lanczos_workspace(s, R, m, rows, field_blocks(s->N), z));
     MBD_TRY(ensure_mesh<T>(s, z.ld));
+    if (full) MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
+    return MBD_OK;
+}
+
+// Algorithm 1 with Algorithm 2 per step: m Lanczos steps for all R probes, the
+// quadrature and the energy, enqueued on s->stream (kernels and memsets only,
+// so the sequence can be captured in a CUDA graph).  seed_dev, when set, is a
+// device word holding the seed (read by the first prologue).
+template <class T>
+mbd_status enqueue_lanczos(mbd_system *s, int R, int m, uint64_t seed, const uint64_t *seed_dev, const Lz &z,
+                           bool full) {
+    const int rows = 3 * s->N;
     PrecData<T> &P = prec<T>(s);
+    MBD_CUDA_TRY(cudaMemsetAsync(s->a.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->b.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
     FieldOut<T> fo;
     fo.mode = kFieldLanczos;
     fo.terms = MBD_TERM_ALL;
@@ -571,7 +583,7 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
     for (int k = 0; k < m; ++k) {
         MBD_STAGE(s, MBD_STAGE_PROLOGUE, 1,
                   launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
-                                    (int)sizeof(T), z.nblk));
+                                    (int)sizeof(T), z.nblk, seed_dev));
         if (fuse3) {
             MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
                       launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
@@ -585,7 +597,6 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
         MBD_STAGE(s, MBD_STAGE_FIELD, 1,
                   launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
     }
-    if (full) MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
               launch_tridiag(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(),
                              full ? s->work2.as<double>() : nullptr, s->status.as<int>(), s->stream,
@@ -593,6 +604,11 @@ template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t 
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
               launch_energy_reduce(s->q.as<double>(), R, rows, s->omega_sum, s->scal.as<double>(), s->stream));
     return MBD_OK;
+}
+
+template <class T> mbd_status run_lanczos(mbd_system *s, int R, int m, uint64_t seed, Lz &z, bool full = false) {
+    MBD_TRY(prepare_lanczos<T>(s, R, m, z, full));
+    return enqueue_lanczos<T>(s, R, m, seed, nullptr, z, full);
 }
 
 mbd_status status_from_bits(int bits) {
@@ -739,6 +755,101 @@ template <class T> mbd_status convolve_impl(mbd_system *s, int nvec, const doubl
     return MBD_OK;
 }
 
+// ---------------------------------------------------------------- batches of systems
+}  // namespace
+}  // namespace mbd
+
+struct mbd_batch {
+    int n = 0;
+    int precision = MBD_FP64;
+    long long total_atoms = 0;
+    cudaStream_t stream = nullptr;        // caller's stream: graph launches and result copies
+    cudaStream_t cap = nullptr;           // capture origin (a capturing stream cannot be the legacy stream)
+    std::vector<mbd_system *> sys;
+    std::vector<cudaStream_t> streams;    // one per member: its branch of the graph
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    mbd::DevBuf seeds_d, out_d;           // [n] seeds; [n][2] (energy, trace) then [n] status words
+    uint64_t *host_seeds = nullptr;
+    unsigned char *host_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long graph_kernels = 0;
+    int gR = 0, gm = 0;
+};
+
+namespace mbd {
+namespace {
+
+void destroy_batch_graph(mbd_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_kernels = 0;
+    b->gR = b->gm = 0;
+}
+
+// Every member's run as one branch: fork from the capture stream, the whole
+// Lanczos run on the member's stream, its energy, trace and status copied into
+// the batch's output block, join back.
+template <class T> mbd_status enqueue_batch(mbd_batch *b, int R, int m, std::vector<Lz> &zs) {
+    const size_t n = (size_t)b->n;
+    double *out = b->out_d.as<double>();
+    int *status = reinterpret_cast<int *>(out + 2 * n);
+    MBD_CUDA_TRY(cudaEventRecord(b->fork, b->cap));
+    for (size_t i = 0; i < n; ++i) {
+        mbd_system *s = b->sys[i];
+        MBD_CUDA_TRY(cudaStreamWaitEvent(s->stream, b->fork, 0));
+        MBD_TRY(enqueue_lanczos<T>(s, R, m, 0, b->seeds_d.as<uint64_t>() + i, zs[i], false));
+        MBD_CUDA_TRY(cudaMemcpyAsync(out + 2 * i, s->scal.ptr, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     s->stream));
+        MBD_CUDA_TRY(cudaMemcpyAsync(status + i, s->status.ptr, sizeof(int), cudaMemcpyDeviceToDevice, s->stream));
+        MBD_CUDA_TRY(cudaEventRecord(b->join[i], s->stream));
+        MBD_CUDA_TRY(cudaStreamWaitEvent(b->cap, b->join[i], 0));
+    }
+    return MBD_OK;
+}
+
+template <class T> mbd_status capture_batch(mbd_batch *b, int R, int m) {
+    destroy_batch_graph(b);
+    std::vector<Lz> zs(b->n);
+    // allocations (and the counters' one-time clearing) happen eagerly, outside the graph
+    for (int i = 0; i < b->n; ++i) {
+        MBD_TRY(prepare_lanczos<T>(b->sys[i], R, m, zs[i], false));
+        MBD_CUDA_TRY(cudaStreamSynchronize(b->sys[i]->stream));
+    }
+    MBD_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    const mbd_status st = enqueue_batch<T>(b, R, m, zs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+    if (st != MBD_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (ce != cudaSuccess) set_last_error("cudaStreamEndCapture", ce);
+        cudaGetLastError();
+        return st != MBD_OK ? st : MBD_ERR_CUDA;
+    }
+    size_t nnodes = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nnodes);
+    std::vector<cudaGraphNode_t> nodes(nnodes);
+    if (e == cudaSuccess && nnodes) e = cudaGraphGetNodes(g, nodes.data(), &nnodes);
+    long long kernels = 0;
+    for (size_t i = 0; e == cudaSuccess && i < nnodes; ++i) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[i], &t);
+        kernels += (t == cudaGraphNodeTypeKernel);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        set_last_error("graph instantiate", e);
+        cudaGetLastError();
+        return MBD_ERR_CUDA;
+    }
+    b->graph_kernels = kernels;
+    b->gR = R;
+    b->gm = m;
+    return MBD_OK;
+}
+
 mbd_status check_run_args(mbd_system *s, int R, int m, double *energy) {
     if (!s || !energy) return MBD_ERR_INVALID_ARG;
     if (R < 1 || R > (1 << 20) || m < 1 || m > kMaxSteps) return MBD_ERR_INVALID_ARG;
@@ -781,6 +892,117 @@ void mbd_destroy_system(mbd_system *sys) {
     if (sys->host_status) cudaFreeHost(sys->host_status);
     prof_release(sys);
     delete sys;
+}
+
+mbd_status mbd_create_batch(int32_t n_sys, const mbd_system_desc *descs, void *cuda_stream, mbd_batch **out) {
+    if (out == nullptr || descs == nullptr || n_sys < 1) return MBD_ERR_INVALID_ARG;
+    for (int i = 0; i < n_sys; ++i) {
+        MBD_TRY(validate(&descs[i]));
+        if (descs[i].precision != descs[0].precision) return MBD_ERR_INVALID_ARG;
+    }
+    mbd_batch *b = new (std::nothrow) mbd_batch();
+    if (!b) return MBD_ERR_OOM;
+    b->n = n_sys;
+    b->precision = descs[0].precision;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    auto fail = [&](mbd_status st) {
+        mbd_destroy_batch(b);
+        return st;
+    };
+    cudaError_t ce;
+    if ((ce = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess ||
+        (ce = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) {
+        set_last_error("batch stream", ce);
+        cudaGetLastError();
+        return fail(ce == cudaErrorMemoryAllocation ? MBD_ERR_OOM : MBD_ERR_CUDA);
+    }
+    b->sys.assign(n_sys, nullptr);
+    b->streams.assign(n_sys, nullptr);
+    b->join.assign(n_sys, nullptr);
+    for (int i = 0; i < n_sys; ++i) {
+        if ((ce = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking)) != cudaSuccess ||
+            (ce = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming)) != cudaSuccess) {
+            set_last_error("batch member stream", ce);
+            cudaGetLastError();
+            return fail(MBD_ERR_CUDA);
+        }
+        const mbd_status st = create_impl(&descs[i], b->streams[i], &b->sys[i]);
+        if (st != MBD_OK) {
+            b->sys[i] = nullptr;
+            return fail(st);
+        }
+        b->total_atoms += descs[i].n_atoms;
+    }
+    mbd_status st;
+    if ((st = b->seeds_d.ensure(sizeof(uint64_t) * n_sys)) != MBD_OK) return fail(st);
+    if ((st = b->out_d.ensure((2 * sizeof(double) + sizeof(int)) * n_sys)) != MBD_OK) return fail(st);
+    if (cudaMallocHost(&b->host_seeds, sizeof(uint64_t) * n_sys) != cudaSuccess ||
+        cudaMallocHost(&b->host_out, (2 * sizeof(double) + sizeof(int)) * n_sys) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MBD_ERR_OOM);
+    }
+    *out = b;
+    return MBD_OK;
+}
+
+void mbd_destroy_batch(mbd_batch *b) {
+    if (b == nullptr) return;
+    destroy_batch_graph(b);
+    for (mbd_system *s : b->sys) mbd_destroy_system(s);
+    for (cudaStream_t st : b->streams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->host_seeds) cudaFreeHost(b->host_seeds);
+    if (b->host_out) cudaFreeHost(b->host_out);
+    delete b;
+}
+
+mbd_status mbd_batch_lanczos_energy(mbd_batch *b, int32_t R, int32_t m, const uint64_t *seeds, double *energies,
+                                    double *traces, int32_t *failed_member) {
+    if (!b || !seeds || !energies) return MBD_ERR_INVALID_ARG;
+    if (R < 1 || R > (1 << 20) || m < 1 || m > kMaxSteps) return MBD_ERR_INVALID_ARG;
+    if (!b->exec || b->gR != R || b->gm != m) {
+        // work queued on the caller's stream before this call precedes the (eager) workspace setup
+        MBD_CUDA_TRY(cudaStreamSynchronize(b->stream));
+        if (b->precision == MBD_FP64)
+            MBD_TRY(capture_batch<double>(b, R, m));
+        else
+            MBD_TRY(capture_batch<float>(b, R, m));
+    }
+    const size_t n = (size_t)b->n;
+    std::memcpy(b->host_seeds, seeds, sizeof(uint64_t) * n);
+    MBD_CUDA_TRY(cudaMemcpyAsync(b->seeds_d.ptr, b->host_seeds, sizeof(uint64_t) * n, cudaMemcpyHostToDevice,
+                                 b->stream));
+    MBD_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+    MBD_CUDA_TRY(cudaMemcpyAsync(b->host_out, b->out_d.ptr, (2 * sizeof(double) + sizeof(int)) * n,
+                                 cudaMemcpyDeviceToHost, b->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    const double *res = reinterpret_cast<const double *>(b->host_out);
+    const int *bits = reinterpret_cast<const int *>(res + 2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        mbd_status st = status_from_bits(bits[i]);
+        if (st == MBD_OK && !std::isfinite(res[2 * i])) st = MBD_ERR_NONFINITE;
+        if (st != MBD_OK) {
+            if (failed_member) *failed_member = (int32_t)i;
+            return st;
+        }
+    }
+    for (size_t i = 0; i < n; ++i) {
+        energies[i] = res[2 * i];
+        if (traces) traces[i] = res[2 * i + 1];
+    }
+    return MBD_OK;
+}
+
+mbd_status mbd_batch_get_info(const mbd_batch *b, mbd_batch_info *info) {
+    if (!b || !info) return MBD_ERR_INVALID_ARG;
+    info->n_sys = b->n;
+    info->graph_kernels = b->graph_kernels;
+    info->total_atoms = b->total_atoms;
+    return MBD_OK;
 }
 
 mbd_status mbd_update_positions(mbd_system *s, const double *pos) {

@@ -267,7 +267,8 @@ template <class T> mbd_status launch_field(mbd_system *s, const T *d, const T *m
 
 // Lanczos
 mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int m, uint64_t seed, int R, int ld,
-                             int rows, const double *g, void *dout, int dtype_bytes, int nblk);
+                             int rows, const double *g, void *dout, int dtype_bytes, int nblk,
+                             const uint64_t *seed_dev = nullptr);
 // q [R] and, when coef != nullptr, c = Delta^{-1/2} e_1 as coef [m][ld]
 mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
                           double *coef, int *status, cudaStream_t st, bool df64 = false);

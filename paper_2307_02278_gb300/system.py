@@ -7,13 +7,13 @@ of layout [nvec][N][3] (or [nvec][3N]).
 from __future__ import annotations
 
 import ctypes
-from ctypes import byref, c_double, c_void_p
+from ctypes import byref, c_double, c_int32, c_uint64, c_void_p
 
 import numpy as np
 import torch
 
-from ._abi import (MBD_EIGEN_DF64, MBD_EIGEN_FP64, MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES, Info, Profile,
-                   SystemDesc, check, lib)
+from ._abi import (MBD_EIGEN_DF64, MBD_EIGEN_FP64, MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES, BatchInfo, Info,
+                   Profile, SystemDesc, check, lib)
 
 PRECISIONS = {"fp64": MBD_FP64, "mixed": MBD_MIXED}
 EIGEN = {"fp64": MBD_EIGEN_FP64, "df64": MBD_EIGEN_DF64}
@@ -29,6 +29,40 @@ def _cuda_f64(t: torch.Tensor, name: str) -> torch.Tensor:
     return t.contiguous()
 
 
+def _make_desc(cell, pos, alpha, omega, r_vdw, *, damp_beta=0.83, damp_d=6.0, ewald_beta=0.35, r_cut=10.0,
+               damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64", eigen_precision="fp64"):
+    """An mbd_system_desc and the host arrays it points to (keep them alive while it is used)."""
+    keep = [np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3),
+            np.ascontiguousarray(alpha, dtype=np.float64), np.ascontiguousarray(omega, dtype=np.float64),
+            np.ascontiguousarray(r_vdw, dtype=np.float64)]
+    d = SystemDesc()
+    d.n_atoms = int(keep[0].shape[0])
+    d.cell[:] = [float(x) for x in np.asarray(cell, dtype=np.float64).ravel()]
+    d.pos, d.alpha, d.omega, d.r_vdw = (_dptr(x) for x in keep)
+    d.damp_beta, d.damp_d, d.ewald_beta = float(damp_beta), float(damp_d), float(ewald_beta)
+    d.r_cut, d.damp_cut = float(r_cut), float(damp_cut)
+    d.mesh[:] = [int(k) for k in mesh]
+    d.spline_order = int(spline_order)
+    d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    d.eigen_precision = EIGEN[eigen_precision] if isinstance(eigen_precision, str) else int(eigen_precision)
+    return d, keep
+
+
+def _workload_kw(s) -> dict:
+    return dict(damp_beta=s.damp_beta, damp_d=s.damp_d, ewald_beta=s.ewald_beta, r_cut=s.r_cut,
+                damp_cut=s.damp_cut, mesh=s.mesh, spline_order=s.spline_order)
+
+
+def _stream(stream):
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream()
+    return stream
+
+
+def _stream_handle(stream):
+    return c_void_p(stream.cuda_stream if stream is not None else 0)
+
+
 class MBDSystem:
     """One periodic system on the GPU (mbd_create_system)."""
 
@@ -36,39 +70,22 @@ class MBDSystem:
                  r_cut=10.0, damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64",
                  eigen_precision="fp64", stream=None):
         self._handle = None
-        self.n_atoms = int(np.asarray(pos).shape[0])
-        self._pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-        self._alpha = np.ascontiguousarray(alpha, dtype=np.float64)
-        self._omega = np.ascontiguousarray(omega, dtype=np.float64)
-        self._rvdw = np.ascontiguousarray(r_vdw, dtype=np.float64)
-        d = SystemDesc()
-        d.n_atoms = self.n_atoms
-        d.cell[:] = [float(x) for x in np.asarray(cell, dtype=np.float64).ravel()]
-        d.pos = _dptr(self._pos)
-        d.alpha = _dptr(self._alpha)
-        d.omega = _dptr(self._omega)
-        d.r_vdw = _dptr(self._rvdw)
-        d.damp_beta, d.damp_d, d.ewald_beta = float(damp_beta), float(damp_d), float(ewald_beta)
-        d.r_cut, d.damp_cut = float(r_cut), float(damp_cut)
-        d.mesh[:] = [int(k) for k in mesh]
-        d.spline_order = int(spline_order)
-        d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        d.eigen_precision = EIGEN[eigen_precision] if isinstance(eigen_precision, str) else int(eigen_precision)
+        d, self._keep = _make_desc(cell, pos, alpha, omega, r_vdw, damp_beta=damp_beta, damp_d=damp_d,
+                                   ewald_beta=ewald_beta, r_cut=r_cut, damp_cut=damp_cut, mesh=mesh,
+                                   spline_order=spline_order, precision=precision,
+                                   eigen_precision=eigen_precision)
+        self.n_atoms = d.n_atoms
+        self._pos = self._keep[0]
         self.precision = precision
-        if stream is None and torch.cuda.is_available():
-            stream = torch.cuda.current_stream()
-        self.stream = stream
-        sh = c_void_p(stream.cuda_stream if stream is not None else 0)
+        self.stream = _stream(stream)
         out = c_void_p()
-        check(lib().mbd_create_system(byref(d), sh, byref(out)), "mbd_create_system")
+        check(lib().mbd_create_system(byref(d), _stream_handle(self.stream), byref(out)), "mbd_create_system")
         self._handle = out
 
     @classmethod
     def from_workload(cls, s, precision="fp64", **kw):
         """Build from a workloads.System-like object (attributes of the same names)."""
-        return cls(s.cell, s.pos, s.alpha, s.omega, s.r_vdw, damp_beta=s.damp_beta, damp_d=s.damp_d,
-                   ewald_beta=s.ewald_beta, r_cut=s.r_cut, damp_cut=s.damp_cut, mesh=s.mesh,
-                   spline_order=s.spline_order, precision=precision, **kw)
+        return cls(s.cell, s.pos, s.alpha, s.omega, s.r_vdw, precision=precision, **_workload_kw(s), **kw)
 
     # ------------------------------------------------------------------ lifetime
     def close(self):
@@ -162,6 +179,65 @@ class MBDSystem:
         check(lib().mbd_energy_forces(self._handle, n_probes, n_steps, seed, byref(e), forces.data_ptr()),
               "mbd_energy_forces")
         return e.value, forces
+
+
+class MBDBatch:
+    """Independent periodic systems of uneven sizes run together (mbd_create_batch):
+    every member's Lanczos run is one branch of a CUDA graph recorded on the first
+    call with a given (n_probes, n_steps) and replayed afterwards."""
+
+    def __init__(self, systems, precision="mixed", eigen_precision="fp64", stream=None):
+        self._handle = None
+        descs = (SystemDesc * len(systems))()
+        self._keep = []
+        for i, s in enumerate(systems):
+            d, keep = _make_desc(s.cell, s.pos, s.alpha, s.omega, s.r_vdw, precision=precision,
+                                 eigen_precision=eigen_precision, **_workload_kw(s))
+            descs[i] = d
+            self._keep.append(keep)
+        self.n_sys = len(systems)
+        self.stream = _stream(stream)
+        out = c_void_p()
+        check(lib().mbd_create_batch(self.n_sys, descs, _stream_handle(self.stream), byref(out)),
+              "mbd_create_batch")
+        self._handle = out
+
+    def close(self):
+        if self._handle is not None:
+            lib().mbd_destroy_batch(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        check(lib().mbd_batch_get_info(self._handle, byref(i)), "mbd_batch_get_info")
+        return dict(n_sys=i.n_sys, graph_kernels=i.graph_kernels, total_atoms=i.total_atoms)
+
+    def lanczos_energy(self, n_probes: int, n_steps: int, seeds):
+        """(energies [n_sys], traces [n_sys]) with member i on seeds[i]."""
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        if sd.shape != (self.n_sys,):
+            raise ValueError(f"seeds must have shape ({self.n_sys},)")
+        e = np.zeros(self.n_sys)
+        t = np.zeros(self.n_sys)
+        bad = c_int32(-1)
+        code = lib().mbd_batch_lanczos_energy(self._handle, n_probes, n_steps,
+                                              sd.ctypes.data_as(ctypes.POINTER(c_uint64)), _dptr(e), _dptr(t),
+                                              byref(bad))
+        where = "mbd_batch_lanczos_energy" + (f" (member {bad.value})" if bad.value >= 0 else "")
+        check(code, where)
+        return e, t
 
 
 def generate_probes(seed: int, n_probes: int, dim: int, first: int = 0) -> torch.Tensor:
