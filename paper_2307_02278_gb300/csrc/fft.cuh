@@ -1,0 +1,484 @@
+// Mesh-stage device code shared by the operator kernels (kernels_mesh.cu) and
+// the compile-time FFT passes (fft_sizes_*.cu): vector loads, complex
+// arithmetic, the in-register DFTs, the Stockham passes with compile-time
+// mesh size, and the spreading fused with the first forward pass.
+#pragma once
+
+#include "mbd_internal.cuh"
+
+namespace mbd {
+
+template <class T> struct FFTArgs {
+    typename Cplx<T>::type *data;   // complex view of the mesh
+    const typename Cplx<T>::type *tw;   // exp(-2 pi i n / K), n = 0..K-1
+    const T *G;          // influence function (fused pass only)
+    int K;
+    int inner;           // complex elements per row (contiguous)
+    int W;               // tile width (complex columns)
+    int nst;
+    unsigned long long radices;   // stage s radix = (radices >> 4 s) & 15
+    int V;               // complex probe pairs per mesh point (fused pass: G index = e / V)
+    int sign;            // -1 forward, +1 inverse (unfused passes)
+};
+
+// Compile-time passes for the smooth sizes listed below (fft_sizes_*.cu).
+// Return 1 when launched, 0 when the launch could not be configured, -1 when
+// there is no compile-time pass for the size or tile width asked for.
+//   a.W: the tile width; float passes exist for W = 32 (all passes) and
+//   W = 16 (unfused), double passes for W = 16.
+template <class T> int launch_fft_ct_sized(const FFTArgs<T> &a, bool fused, unsigned grid, cudaStream_t st);
+//   W: the tile width of the fused spreading (float 32 or 16, double 16).
+template <class T>
+int launch_sf3_sized(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row,
+                     const SpreadRec<T> *rec, const typename Cplx<T>::type *tw, cudaStream_t st);
+bool fft_ct_size(int K);
+
+// Sizes with a compile-time pass and their radices (first stage first), in
+// groups of one translation unit each.
+#define MBD_FFT_GROUP0(X) X(16, 4, 4) X(18, 3, 3, 2) X(20, 5, 4) X(24, 8, 3) X(25, 5, 5) X(27, 3, 3, 3) X(30, 5, 3, 2)
+#define MBD_FFT_GROUP1(X) X(32, 8, 4) X(36, 4, 3, 3) X(40, 8, 5) X(45, 5, 3, 3) X(48, 4, 4, 3) X(50, 5, 5, 2) \
+    X(54, 3, 3, 3, 2)
+#define MBD_FFT_GROUP2(X) X(60, 5, 4, 3) X(64, 8, 8) X(72, 8, 3, 3) X(75, 5, 5, 3) X(80, 5, 4, 4) \
+    X(81, 3, 3, 3, 3) X(90, 5, 3, 3, 2)
+#define MBD_FFT_GROUP3(X) X(96, 8, 4, 3) X(100, 5, 5, 4) X(108, 4, 3, 3, 3) X(120, 8, 5, 3) X(125, 5, 5, 5) \
+    X(128, 8, 8, 2) X(135, 5, 3, 3, 3)
+#define MBD_FFT_GROUP4(X) X(144, 4, 4, 3, 3) X(150, 5, 5, 3, 2) X(160, 8, 5, 4) X(162, 3, 3, 3, 3, 2) \
+    X(180, 5, 4, 3, 3) X(192, 8, 8, 3) X(200, 8, 5, 5)
+#define MBD_FFT_GROUP5(X) X(216, 8, 3, 3, 3) X(225, 5, 5, 3, 3) X(240, 5, 4, 4, 3) X(243, 3, 3, 3, 3, 3) \
+    X(250, 5, 5, 5, 2) X(256, 8, 8, 4)
+#define MBD_FFT_NUM_GROUPS 6
+
+template <class T> int launch_fft_ct_group0(const FFTArgs<T> &, bool, unsigned, cudaStream_t);
+template <class T> int launch_fft_ct_group1(const FFTArgs<T> &, bool, unsigned, cudaStream_t);
+template <class T> int launch_fft_ct_group2(const FFTArgs<T> &, bool, unsigned, cudaStream_t);
+template <class T> int launch_fft_ct_group3(const FFTArgs<T> &, bool, unsigned, cudaStream_t);
+template <class T> int launch_fft_ct_group4(const FFTArgs<T> &, bool, unsigned, cudaStream_t);
+template <class T> int launch_fft_ct_group5(const FFTArgs<T> &, bool, unsigned, cudaStream_t);
+#define MBD_SF3_DECL(g)                                                                                          \
+    template <class T>                                                                                           \
+    int launch_sf3_group##g(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row, \
+                            const SpreadRec<T> *rec, const typename Cplx<T>::type *tw, cudaStream_t st);
+MBD_SF3_DECL(0)
+MBD_SF3_DECL(1)
+MBD_SF3_DECL(2)
+MBD_SF3_DECL(3)
+MBD_SF3_DECL(4)
+MBD_SF3_DECL(5)
+#undef MBD_SF3_DECL
+
+namespace {
+
+// Vector loads/stores of VEC consecutive values (VEC in {1, 2, 4}).
+template <class T, int VEC> struct VecT;
+template <> struct VecT<float, 1> { using type = float; };
+template <> struct VecT<float, 2> { using type = float2; };
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<double, 1> { using type = double; };
+template <> struct VecT<double, 2> { using type = double2; };
+
+template <class T, int VEC> __device__ __forceinline__ void vload(const T *p, T *v) {
+    if constexpr (VEC == 4 && sizeof(T) == 8) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = b.x;
+        v[3] = b.y;
+        return;
+    } else {
+    using V = typename VecT<T, VEC>::type;
+    const V x = *reinterpret_cast<const V *>(p);
+    if constexpr (VEC == 1) {
+        v[0] = x;
+    } else if constexpr (VEC == 2) {
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    }
+    }
+}
+template <class T, int VEC> __device__ __forceinline__ void vstore(T *p, const T *v) {
+    if constexpr (VEC == 4 && sizeof(T) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+        return;
+    } else {
+    using V = typename VecT<T, VEC>::type;
+    V x;
+    if constexpr (VEC == 1) {
+        x = v[0];
+    } else if constexpr (VEC == 2) {
+        x.x = v[0];
+        x.y = v[1];
+    } else {
+        x.x = v[0];
+        x.y = v[1];
+        x.z = v[2];
+        x.w = v[3];
+    }
+    *reinterpret_cast<V *>(p) = x;
+    }
+}
+
+// ---------------------------------------------------------------- FFT
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+    return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+// multiply by -i*sign... rot(a) = sign * i * a, with sign = -1 (forward) or +1 (inverse)
+template <class C> __device__ __forceinline__ C rot(C a, int sign) {
+    return sign < 0 ? C{a.y, -a.x} : C{-a.y, a.x};
+}
+
+// In-register R-point DFT  X_t = sum_q x_q exp(sign 2 pi i q t / R), R in {2,3,4,5,8}.
+template <class T, class C> __device__ __forceinline__ void dft2(C *v) {
+    const C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+template <class T, class C> __device__ __forceinline__ void dft4(C *v, int sign) {
+    const C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const C s13 = cadd(v[1], v[3]), d13 = rot(csub(v[1], v[3]), sign);
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+}
+template <class T, class C> __device__ __forceinline__ void dft8(C *v, int sign) {
+    const T h = T(0.70710678118654752440);
+    C e[4] = {v[0], v[2], v[4], v[6]};
+    C o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<T>(e, sign);
+    dft4<T>(o, sign);
+    // twiddles exp(sign 2 pi i t / 8), t = 0..3
+    const C o1 = C{h * (o[1].x - T(sign) * o[1].y), h * (o[1].y + T(sign) * o[1].x)};
+    const C o2 = rot(o[2], sign);
+    const C o3 = C{h * (-o[3].x - T(sign) * o[3].y), h * (-o[3].y + T(sign) * o[3].x)};
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+}
+template <class T, class C> __device__ __forceinline__ void dft3(C *v, int sign) {
+    const T c = T(-0.5), s = T(sign) * T(0.86602540378443864676);
+    const C a = v[0], b = v[1], d = v[2];
+    const C t = cadd(b, d);
+    const C u = csub(b, d);
+    v[0] = cadd(a, t);
+    const C m = C{a.x + c * t.x, a.y + c * t.y};
+    const C n = C{-s * u.y, s * u.x};   // i s (b - d)
+    v[1] = cadd(m, n);
+    v[2] = csub(m, n);
+}
+template <class T, class C> __device__ __forceinline__ void dft5(C *v, int sign) {
+    // cos/sin of 2 pi / 5 and 4 pi / 5
+    const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);
+    const T s1 = T(sign) * T(0.95105651629515357212), s2 = T(sign) * T(0.58778525229247312917);
+    const C a = v[0];
+    const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const C u1 = csub(v[1], v[4]), u2 = csub(v[2], v[3]);
+    v[0] = C{a.x + t1.x + t2.x, a.y + t1.y + t2.y};
+    const C m1 = C{a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y};
+    const C m2 = C{a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y};
+    // i (s1 u1 + s2 u2) and i (s2 u1 - s1 u2)
+    const C n1 = C{-(s1 * u1.y + s2 * u2.y), s1 * u1.x + s2 * u2.x};
+    const C n2 = C{-(s2 * u1.y - s1 * u2.y), s2 * u1.x - s1 * u2.x};
+    v[1] = cadd(m1, n1);
+    v[4] = csub(m1, n1);
+    v[2] = cadd(m2, n2);
+    v[3] = csub(m2, n2);
+}
+
+
+
+template <class T, class C, int R> __device__ __forceinline__ void dft(C *v, int sign) {
+    if constexpr (R == 2) dft2<T>(v);
+    else if constexpr (R == 3) dft3<T>(v, sign);
+    else if constexpr (R == 4) dft4<T>(v, sign);
+    else if constexpr (R == 5) dft5<T>(v, sign);
+    else dft8<T>(v, sign);
+}
+
+// ---------------------------------------------------------------- compile-time passes
+// Threads of a compile-time pass: enough for the stage with the most
+// butterflies (K / smallest radix rows x W columns), at most 256.
+template <int R> constexpr int ct_rmin() { return R; }
+template <int R, int S, int... RS> constexpr int ct_rmin() {
+    return R < ct_rmin<S, RS...>() ? R : ct_rmin<S, RS...>();
+}
+template <int K, int W, int... RS> constexpr int ct_threads() {
+    return (K / ct_rmin<RS...>()) * W >= 256 ? 256 : (((K / ct_rmin<RS...>()) * W + 31) / 32) * 32;
+}
+
+// One radix-R Stockham stage over the K rows of a K x W tile with K, W, the
+// stage's stride NS and the block size NT compile-time, so the index
+// arithmetic folds away and each butterfly stays in registers.  The stage reads
+// the global tile (IN_G, columns >= wc read as zero) or shared memory, and
+// writes the global tile (OUT_G, columns < wc only) or shared memory,
+// multiplying by G on the way out (MULG; G index row * gstride + (c0 + col) / V).
+template <class T, class C, int R, int K, int W, int NT, int NS, bool IN_G, bool OUT_G, bool MULG>
+__device__ __forceinline__ void ct_stage(const C *__restrict__ in_s, const C *__restrict__ in_g, C *__restrict__ out_s,
+                                         C *__restrict__ out_g, size_t gs, int wc, const C *__restrict__ tw, int sign,
+                                         const T *__restrict__ G, size_t gstride, int c0, int V) {
+    constexpr int nb = K / R;
+    constexpr int step = K / (NS * R);
+    constexpr int total = nb * W;
+#pragma unroll
+    for (int it = 0; it < (total + NT - 1) / NT; ++it) {
+        const int idx = it * NT + (int)threadIdx.x;
+        if (total % NT != 0 && idx >= total) break;
+        const int j = idx / W, col = idx % W;
+        C v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            if (IN_G)
+                v[q] = col < wc ? in_g[(size_t)(j + q * nb) * gs + col] : C{T(0), T(0)};
+            else
+                v[q] = in_s[(j + q * nb) * W + col];
+        }
+        const int jm = j % NS;
+        if (NS > 1 && jm != 0) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C t = tw[q * jm * step];
+                if (sign > 0) t.y = -t.y;
+                v[q] = cmul(v[q], t);
+            }
+        }
+        dft<T, C, R>(v, sign);
+        const int base = (j / NS) * NS * R + jm;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int row = base + q * NS;
+            if (MULG && col < wc) {
+                const T gv = G[(size_t)row * gstride + (c0 + col) / V];
+                v[q].x *= gv;
+                v[q].y *= gv;
+            }
+            if (OUT_G) {
+                if (col < wc) out_g[(size_t)row * gs + col] = v[q];
+            } else {
+                out_s[row * W + col] = v[q];
+            }
+        }
+    }
+}
+
+// A run of stages: the first reads the global tile (IN_G) or shared buffer
+// sin, intermediate results ping-pong between the shared buffers, the last
+// writes the global tile (OUT_G) or shared memory, multiplying by G (MULG).
+// Returns the shared buffer holding the result when it stays in shared memory.
+template <class T, class C, int K, int W, int NT, int NS, bool IN_G, bool OUT_G, bool MULG, int R, int... RS>
+__device__ __forceinline__ C *ct_pipe(const C *gin, C *gout, size_t gs, int wc, C *sin, C *sout, const C *tw, int sign,
+                                      const T *G, size_t gstride, int c0, int V) {
+    constexpr bool last = sizeof...(RS) == 0;
+    ct_stage<T, C, R, K, W, NT, NS, IN_G, last && OUT_G, last && MULG>(sin, gin, sout, gout, gs, wc, tw, sign, G,
+                                                                       gstride, c0, V);
+    if constexpr (last) {
+        return sout;
+    } else {
+        __syncthreads();
+        return ct_pipe<T, C, K, W, NT, NS * R, false, OUT_G, MULG, RS...>(gin, gout, gs, wc, sout, sin, tw, sign, G,
+                                                                           gstride, c0, V);
+    }
+}
+
+// One 1D pass along the middle axis of [outer][K][inner] (complex) with
+// compile-time K, W and radices (at least two stages): a block owns one
+// K x W tile.  The first stage loads the global tile straight into registers
+// and the last one stores straight from registers, so shared memory carries
+// only the exchanges between stages; the fused pass (forward, x G, inverse)
+// multiplies by G in the last forward stage.
+template <class T, bool FUSED, int K, int W, int NT, int... RS>
+__global__ void __launch_bounds__(NT) k_fft_ct(FFTArgs<T> a) {
+    using C = typename Cplx<T>::type;
+    static_assert(sizeof...(RS) >= 2, "single-stage sizes would read and write the same global tile");
+    extern __shared__ __align__(16) unsigned char smem_ct[];
+    C *buf0 = reinterpret_cast<C *>(smem_ct), *buf1 = buf0 + K * W;
+    C *tw = buf1 + K * W;
+    for (int i = threadIdx.x; i < K; i += NT) tw[i] = a.tw[i];
+    __syncthreads();
+    const int ncb = (a.inner + W - 1) / W;
+    const size_t outer = blockIdx.x / ncb;
+    const int c0 = (int)(blockIdx.x % ncb) * W;
+    const int wc = min(W, a.inner - c0);
+    C *base = a.data + outer * (size_t)K * a.inner + c0;
+    const size_t gstride = (size_t)(a.inner / a.V);
+    if (FUSED) {
+        C *res = ct_pipe<T, C, K, W, NT, 1, true, false, true, RS...>(base, base, a.inner, wc, buf0, buf1, tw, -1,
+                                                                       a.G, gstride, c0, a.V);
+        __syncthreads();
+        C *other = (res == buf0) ? buf1 : buf0;
+        ct_pipe<T, C, K, W, NT, 1, false, true, false, RS...>(base, base, a.inner, wc, res, other, tw, +1, a.G,
+                                                               gstride, c0, a.V);
+    } else {
+        ct_pipe<T, C, K, W, NT, 1, true, true, false, RS...>(base, base, a.inner, wc, buf0, buf1, tw, a.sign, a.G,
+                                                              gstride, c0, a.V);
+    }
+}
+
+template <class T, bool FUSED, int K, int W, int... RS> int launch_ct(const FFTArgs<T> &a, unsigned grid,
+                                                                      cudaStream_t st) {
+    using C = typename Cplx<T>::type;
+    constexpr int NT = ct_threads<K, W, RS...>();
+    const size_t smem = sizeof(C) * (2 * (size_t)K * W + K);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_fft_ct<T, FUSED, K, W, NT, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    k_fft_ct<T, FUSED, K, W, NT, RS...><<<grid, NT, smem, st>>>(a);
+    return 1;
+}
+
+// The passes of one size: float tiles of 32 (all passes) or 16 (unfused)
+// complex columns, double tiles of 16.
+template <class T, int K, int... RS> int ct_size(const FFTArgs<T> &a, bool fused, unsigned grid, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (a.W == 32) return fused ? launch_ct<T, true, K, 32, RS...>(a, grid, st)
+                                    : launch_ct<T, false, K, 32, RS...>(a, grid, st);
+        if (a.W == 16 && !fused) return launch_ct<T, false, K, 16, RS...>(a, grid, st);
+    } else {
+        if (a.W == 16) return fused ? launch_ct<T, true, K, 16, RS...>(a, grid, st)
+                                    : launch_ct<T, false, K, 16, RS...>(a, grid, st);
+    }
+    return -1;
+}
+
+// Spreading fused with the forward FFT along k3: a block owns one (k1, k2)
+// pencil of K mesh points and W complex probe-pair columns.  The block's
+// 32 / W row chains per warp spread rows k3 = chain, chain + NSG, ... (two
+// rows per iteration: two independent load chains) straight into the
+// shared-memory tile, with the records and order of k_spread_csr; then the
+// block transforms the tile along k3 and writes it once.  Probe columns >= R
+// are masked to zero.
+template <class T, int K, int W, int NT, int... RS>
+__global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typename Cplx<T>::type *__restrict__ mesh,
+                                                    int R, int ld, int K2, const int *__restrict__ row,
+                                                    const SpreadRec<T> *__restrict__ rec,
+                                                    const typename Cplx<T>::type *__restrict__ twg) {
+    using C = typename Cplx<T>::type;
+    static_assert(32 % W == 0, "a warp holds whole row chains");
+    constexpr int G = 32 / W;                 // row chains per warp
+    constexpr int NSG = (NT / 32) * G;        // row chains per block
+    extern __shared__ __align__(16) unsigned char smem_sf[];
+    C *buf0 = reinterpret_cast<C *>(smem_sf);
+    C *buf1 = buf0 + K * W;
+    C *tw = buf1 + K * W;
+    for (int i = threadIdx.x; i < K; i += NT) tw[i] = twg[i];
+    const int V = ld / 2;
+    const int ncb = (V + W - 1) / W;
+    const size_t pencil = blockIdx.x / ncb;              // k1 * K2 + k2
+    const int c0 = (int)(blockIdx.x % ncb) * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cl = lane % W, chain = warp * G + lane / W;
+    const int col = c0 + cl;                             // complex column = probes 2 col, 2 col + 1
+    const bool on = col < V;
+    const T m0 = (2 * col < R) ? T(1) : T(0), m1 = (2 * col + 1 < R) ? T(1) : T(0);
+    for (int k3 = chain; k3 < K; k3 += 2 * NSG) {
+        const int kb = k3 + NSG;
+        const size_t pa = pencil * K + k3, pb = pencil * K + kb;
+        int qa = row[pa];
+        const int qa1 = row[pa + 1];
+        int qb = 0, qb1 = 0;
+        if (kb < K) {
+            qb = row[pb];
+            qb1 = row[pb + 1];
+        }
+        T ax = T(0), ay = T(0), bx = T(0), by = T(0);
+        while (qa < qa1 || qb < qb1) {
+            if (qa < qa1) {
+                const SpreadRec<T> w = rec[qa++];
+                if (on) {
+                    T x[2], y[2], z[2];
+                    const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
+                    vload<T, 2>(dj, x);
+                    vload<T, 2>(dj + ld, y);
+                    vload<T, 2>(dj + 2 * (size_t)ld, z);
+                    ax += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
+                    ay += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+                }
+            }
+            if (qb < qb1) {
+                const SpreadRec<T> w = rec[qb++];
+                if (on) {
+                    T x[2], y[2], z[2];
+                    const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
+                    vload<T, 2>(dj, x);
+                    vload<T, 2>(dj + ld, y);
+                    vload<T, 2>(dj + 2 * (size_t)ld, z);
+                    bx += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
+                    by += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+                }
+            }
+        }
+        buf0[k3 * W + cl] = on ? C{ax * m0, ay * m1} : C{T(0), T(0)};
+        if (kb < K) buf0[kb * W + cl] = on ? C{bx * m0, by * m1} : C{T(0), T(0)};
+    }
+    __syncthreads();
+    const int wc = min(W, V - c0);
+    C *base = mesh + pencil * (size_t)K * V + c0;
+    ct_pipe<T, C, K, W, NT, 1, false, true, false, RS...>(base, base, (size_t)V, wc, buf0, buf1, tw, -1,
+                                                           (const T *)nullptr, 0, c0, V);
+}
+
+template <class T, int K, int W, int... RS>
+int launch_sf3(const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row, const SpreadRec<T> *rec,
+               const typename Cplx<T>::type *tw, cudaStream_t st) {
+    using C = typename Cplx<T>::type;
+    constexpr int NT = ct_threads<K, W, RS...>();
+    const size_t smem = sizeof(C) * (2 * (size_t)K * W + K);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_spread_fft3<T, K, W, NT, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    const int V = ld / 2;
+    const unsigned grid = (unsigned)((size_t)K1 * K2 * ((V + W - 1) / W));
+    k_spread_fft3<T, K, W, NT, RS...><<<grid, NT, smem, st>>>(d, reinterpret_cast<C *>(mesh), R, ld, K2, row, rec,
+                                                              tw);
+    return 1;
+}
+
+template <class T, int K, int... RS>
+int sf3_size(int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row, const SpreadRec<T> *rec,
+             const typename Cplx<T>::type *tw, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (W == 32) return launch_sf3<T, K, 32, RS...>(d, mesh, R, ld, K1, K2, row, rec, tw, st);
+        if (W == 16) return launch_sf3<T, K, 16, RS...>(d, mesh, R, ld, K1, K2, row, rec, tw, st);
+    } else {
+        if (W == 16) return launch_sf3<T, K, 16, RS...>(d, mesh, R, ld, K1, K2, row, rec, tw, st);
+    }
+    return -1;
+}
+
+}  // namespace
+
+// The translation unit of group g: dispatch over its sizes.
+#define MBD_CT_CASE(K, ...) \
+    case K: return ct_size<T, K, __VA_ARGS__>(a, fused, grid, st);
+#define MBD_SF3_CASE(K, ...) \
+    case K: return sf3_size<T, K, __VA_ARGS__>(W, d, mesh, R, ld, K1, K2, row, rec, tw, st);
+#define MBD_FFT_GROUP_TU(g)                                                                                       \
+    template <class T> int launch_fft_ct_group##g(const FFTArgs<T> &a, bool fused, unsigned grid, cudaStream_t st) { \
+        switch (a.K) { MBD_FFT_GROUP##g(MBD_CT_CASE) default: return -1; }                                         \
+    }                                                                                                              \
+    template <class T>                                                                                             \
+    int launch_sf3_group##g(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row,    \
+                            const SpreadRec<T> *rec, const typename Cplx<T>::type *tw, cudaStream_t st) {          \
+        switch (K3) { MBD_FFT_GROUP##g(MBD_SF3_CASE) default: return -1; }                                         \
+    }                                                                                                              \
+    template int launch_fft_ct_group##g<float>(const FFTArgs<float> &, bool, unsigned, cudaStream_t);              \
+    template int launch_fft_ct_group##g<double>(const FFTArgs<double> &, bool, unsigned, cudaStream_t);            \
+    template int launch_sf3_group##g<float>(int, int, const float *, float *, int, int, int, int, const int *,     \
+                                            const SpreadRec<float> *, const float2 *, cudaStream_t);               \
+    template int launch_sf3_group##g<double>(int, int, const double *, double *, int, int, int, int, const int *,  \
+                                             const SpreadRec<double> *, const double2 *, cudaStream_t);
+
+}  // namespace mbd
