@@ -444,6 +444,13 @@ mbd_status create_impl(const mbd_system_desc *d, void *stream, mbd_system **out)
     s->precision = d->precision;
     s->eigen_df64 = d->eigen_precision == MBD_EIGEN_DF64 ? 1 : 0;
     s->stream = static_cast<cudaStream_t>(stream);
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            s->num_sms = nsm;
+        cudaGetLastError();
+    }
     const size_t n = (size_t)s->N;
     s->alpha.assign(d->alpha, d->alpha + n);
     s->omega.assign(d->omega, d->omega + n);
@@ -554,7 +561,7 @@ template <class T> mbd_status ensure_mesh(mbd_system *s, int ld) {
 // Workspace for an m-step run with R probes (allocations only: eager).
 template <class T> mbd_status prepare_lanczos(mbd_system *s, int R, int m, Lz &z, bool full) {
     const int rows = 3 * s->N;
-    MBD_TRY(lanczos_workspace(s, R, m, rows, field_blocks(s->N), z));
+    MBD_TRY(lanczos_workspace(s, R, m, rows, field_blocks(s, probe_ld(R)), z));
     MBD_TRY(ensure_mesh<T>(s, z.ld));
     if (full) MBD_TRY(s->work2.ensure(sizeof(double) * (size_t)m * z.ld));
     return MBD_OK;

@@ -684,9 +684,9 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     a.w2 = s->w2_d.as<double>();
     a.self_coef = -4.0 * s->ewald_beta * s->ewald_beta * s->ewald_beta / (3.0 * 1.77245385090551602730);
     a.o = o;
-    const int vec = (sizeof(T) == 4 && ld % 4 == 0 && ld >= 128) ? 4 : ((ld % 2 == 0 && ld >= 64) ? 2 : 1);
-    const int apb = field_apb(s->N);
-    dim3 grid(field_blocks(s->N), (ld + 32 * vec - 1) / (32 * vec));
+    const int vec = field_vec(ld, (int)sizeof(T));
+    const int apb = field_apb(s, ld);
+    dim3 grid(field_blocks(s, ld), (ld + 32 * vec - 1) / (32 * vec));
 #define MBD_FIELD_LAUNCH(V, P) k_field<T, V, P><<<grid, kWarps * 32, 0, s->stream>>>(a, apb)
     if (vec == 4) {
         if constexpr (sizeof(T) == 4) {
@@ -705,9 +705,59 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     return MBD_OK;
 }
 
-// Atoms per block of the field kernel: about four blocks per SM.
-int field_apb(int N) { return std::max(1, std::min(64, (N + 152 * 4 - 1) / (152 * 4))); }
-int field_blocks(int N) { return (N + field_apb(N) - 1) / field_apb(N); }
+// Probes per lane of the field kernel.
+int field_vec(int ld, int real_bytes) {
+    return (real_bytes == 4 && ld % 4 == 0 && ld >= 128) ? 4 : ((ld % 2 == 0 && ld >= 64) ? 2 : 1);
+}
+
+namespace {
+// Resident blocks per SM of one field-kernel variant (the same on every
+// device of one architecture), asked of the occupancy calculator once.
+template <class T, int V, int P> int field_occupancy() {
+    static int nb = 0;
+    if (nb == 0) {
+        int x = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, k_field<T, V, P>, kWarps * 32, 0) != cudaSuccess ||
+            x < 1) {
+            cudaGetLastError();
+            x = 1;
+        }
+        nb = x;
+    }
+    return nb;
+}
+
+int field_resident_blocks(const mbd_system *s, int ld) {
+    const bool p6 = s->p == 6;
+    int nb;
+    if (s->precision == MBD_FP64) {
+        const int vec = field_vec(ld, 8);
+        nb = vec == 2 ? (p6 ? field_occupancy<double, 2, 6>() : field_occupancy<double, 2, 0>())
+                      : (p6 ? field_occupancy<double, 1, 6>() : field_occupancy<double, 1, 0>());
+    } else {
+        const int vec = field_vec(ld, 4);
+        nb = vec == 4   ? (p6 ? field_occupancy<float, 4, 6>() : field_occupancy<float, 4, 0>())
+             : vec == 2 ? (p6 ? field_occupancy<float, 2, 6>() : field_occupancy<float, 2, 0>())
+                        : (p6 ? field_occupancy<float, 1, 6>() : field_occupancy<float, 1, 0>());
+    }
+    return nb * std::max(1, s->num_sms);
+}
+}  // namespace
+
+// Atoms per block of the field kernel: the blocks fill whole waves of the
+// resident-block capacity (blocks per SM x SMs, shared by the probe chunks),
+// with at most 64 atoms per block (more waves beyond that, for balance).
+int field_apb(const mbd_system *s, int ld) {
+    const int vec = field_vec(ld, s->precision == MBD_FP64 ? 8 : 4);
+    const int ych = (ld + 32 * vec - 1) / (32 * vec);
+    const long long per_wave = std::max(1, field_resident_blocks(s, ld) / ych);
+    const long long waves = (s->N + 64 * per_wave - 1) / (64 * per_wave);
+    return (int)std::max<long long>(1, (s->N + waves * per_wave - 1) / (waves * per_wave));
+}
+int field_blocks(const mbd_system *s, int ld) {
+    const int apb = field_apb(s, ld);
+    return (s->N + apb - 1) / apb;
+}
 
 template mbd_status build_spread_matrix<double>(mbd_system *);
 template mbd_status build_spread_matrix<float>(mbd_system *);

@@ -211,6 +211,7 @@ struct mbd_system {
     double ewald_beta, r_cut, damp_cut, damp_beta, damp_d;
     int precision;
     int eigen_df64;     // tridiagonal eigensolve in double-float instead of FP64
+    int num_sms = 1;    // multiprocessors of the device the system lives on
     cudaStream_t stream;
     double omega_sum;
     mbd::FFTDim fft[3];
@@ -276,8 +277,9 @@ mbd_status launch_energy_reduce(const double *q, int R, int dim, double omega_su
 mbd_status launch_probes(uint64_t seed, int first, int R, int dim, double *v, cudaStream_t st);
 mbd_status launch_dense_step(const double *c, int dim, const LanczosView &lz, int k, int R, int ld, int nblk,
                              cudaStream_t st);
-int field_blocks(int N);
-int field_apb(int N);
+int field_vec(int ld, int real_bytes);
+int field_apb(const mbd_system *s, int ld);
+int field_blocks(const mbd_system *s, int ld);
 
 // layout helpers
 mbd_status launch_to_probe_major(const double *x, int nvec, int rows, double *xt, int ld, cudaStream_t st);
