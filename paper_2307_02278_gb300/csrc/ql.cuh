@@ -14,14 +14,22 @@ namespace mbd {
 // deflation threshold for 48-bit arithmetic
 constexpr float kQLEps = 1.42e-14f;
 
-// first m >= l with a negligible off-diagonal e[m] (or n - 1)
-__device__ __forceinline__ int find_split(const df *d, const df *e, int l, int n) {
-    int m = l;
-    for (; m < n - 1; ++m) {
-        const float dd = df_abs_hi(d[m]) + df_abs_hi(d[m + 1]);
-        if (df_abs_hi(e[m]) <= kQLEps * dd) break;
+// First m >= l with a negligible off-diagonal e[m] (or n - 1).  Called by
+// all 32 lanes of a warp: lane t tests m = l + t, l + t + 32, ...
+__device__ __forceinline__ bool negligible(const df *d, const df *e, int m) {
+    return df_abs_hi(e[m]) <= kQLEps * (df_abs_hi(d[m]) + df_abs_hi(d[m + 1]));
+}
+__device__ __forceinline__ bool negligible(const double *d, const double *e, int m) {
+    return fabs(e[m]) <= 2.220446049250313e-16 * (fabs(d[m]) + fabs(d[m + 1]));
+}
+template <class S> __device__ __forceinline__ int find_split(const S *d, const S *e, int l, int n) {
+    const int lane = threadIdx.x & 31;
+    for (int base = l; base < n - 1; base += 32) {
+        const int m = base + lane;
+        const unsigned hit = __ballot_sync(0xffffffffu, m < n - 1 && negligible(d, e, m));
+        if (hit) return base + __ffs(hit) - 1;
     }
-    return m;
+    return n - 1;
 }
 
 // One implicit QL sweep on the block l..mm (Wilkinson shift); records the
@@ -82,15 +90,6 @@ __device__ __forceinline__ void apply_rotations(df *zr, const df *cs, const df *
 }
 
 // ---------------------------------------------------------------- FP64
-__device__ __forceinline__ int find_split(const double *d, const double *e, int l, int n) {
-    const double eps = 2.220446049250313e-16;
-    int m = l;
-    for (; m < n - 1; ++m) {
-        const double dd = fabs(d[m]) + fabs(d[m + 1]);
-        if (fabs(e[m]) <= eps * dd) break;
-    }
-    return m;
-}
 
 __device__ __forceinline__ int ql_sweep(double *d, double *e, double *cs, double *sn, int l, int mm) {
     double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
@@ -98,11 +97,14 @@ __device__ __forceinline__ int ql_sweep(double *d, double *e, double *cs, double
     g = d[mm] - d[l] + e[l] / (g + copysign(rr, g));
     double s = 1.0, c = 1.0, p = 0.0;
     int nrot = 0;
+    // FP64 operations have a long latency on this part: the chain from one
+    // reciprocal square root to the next is kept to five dependent operations.
     for (int i = mm - 1; i >= l; --i) {
         const double f = s * e[i];
         const double b = c * e[i];
+        const double b2 = b + b;
         // r = |(f, g)|, s = f / r, c = g / r with one reciprocal square root
-        const double x = fma(f, f, g * g);
+        const double x = fma(g, g, f * f);
         if (x == 0.0) {
             e[i + 1] = 0.0;
             d[i + 1] -= p;
@@ -115,10 +117,10 @@ __device__ __forceinline__ int ql_sweep(double *d, double *e, double *cs, double
         s = f * inv;
         c = g * inv;
         g = d[i + 1] - p;
-        rr = (d[i] - g) * s + 2.0 * c * b;
+        rr = fma(d[i] - g, s, c * b2);
         p = s * rr;
         d[i + 1] = g + p;
-        g = c * rr - b;
+        g = fma(c, rr, -b);
         cs[i] = c;
         sn[i] = s;
         ++nrot;
