@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--workload", default="water3000", choices=["water3000", "batch64"],
                     help="batch64: the 64 uneven random boxes (200-20000 atoms, 32 probes x 40 steps) run as "
                          "one graph-replayed batch (energies)")
+    ap.add_argument("--study", default="", choices=["", "delta11"],
+                    help="delta11: Delta_11 against the mesh for the 14.2 angstrom water and diamond boxes, "
+                         "and the parameters mbd_spme_params chooses (JSON lines)")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -510,6 +513,57 @@ def run_batch(args, world, rank, local):
     return 0
 
 
+def run_delta11_study(args):
+    """Delta_11 = v^T C v of one normalised Rademacher probe against the mesh
+    (spline orders 4 and 6), for a 96-molecule water box and a 512-atom diamond
+    crystal (both 14.2 angstrom), r_cut 12 bohr, damping cut 13 bohr,
+    beta_E 0.3/bohr, FP64.  Deviations are from the 96-point mesh; times are the
+    device time of one Lanczos step with one probe (CUDA events, median of 20)."""
+    import numpy as np
+    import torch
+
+    from paper_2307_02278_gb300.build import build
+    build()
+    import paper_2307_02278_gb300 as mbd
+    from workloads.systems import ANGSTROM, diamond_system, water_system
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    seed = 2307022781
+
+    def d11_and_ms(s):
+        g = mbd.MBDSystem.from_workload(s, precision="fp64")
+        _, det = g.lanczos_energy(1, 2, seed, details=True)
+        ts = []
+        for _ in range(20):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.lanczos_energy(1, 1, seed)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        g.close()
+        return float(det["a"][0, 0]), float(np.median(ts))
+
+    for name, make in (("water96_L14.2A", lambda: water_system(96, 5)), ("diamond512_L14.3A", diamond_system)):
+        base = make().with_(r_cut=12.0, damp_cut=13.0, ewald_beta=0.3)
+        box_a = base.cell[0, 0] / ANGSTROM
+        for p in (4, 6):
+            ref, _ = d11_and_ms(base.with_(mesh=(96, 96, 96), spline_order=p))
+            for k in (8, 10, 12, 15, 16, 18, 20, 24, 27, 30, 36, 48):
+                if k < 2 * p:
+                    continue
+                d, ms = d11_and_ms(base.with_(mesh=(k, k, k), spline_order=p))
+                print(json.dumps({"study": "delta11_vs_mesh", "system": name, "spline_order": p, "mesh": k,
+                                  "points_per_angstrom": k / box_a, "delta11": d,
+                                  "rel_dev_from_mesh96": abs(d - ref) / abs(ref), "ms_one_step_one_probe": ms}),
+                      flush=True)
+        for tol in (1e-2, 1e-3, 1e-4, 1e-5):
+            c = mbd.spme_params(base, tol, 6)
+            print(json.dumps({"study": "spme_params", "system": name, "tol": tol, **c}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_env()
@@ -518,6 +572,8 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.study == "delta11":
+        return run_delta11_study(args)
     if args.workload == "batch64":
         return run_batch(args, world, rank, local)
     return run_ours(args, world, rank, local)

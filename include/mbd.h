@@ -135,6 +135,40 @@ mbd_status mbd_lanczos_energy(mbd_system *sys, int32_t n_probes, int32_t n_steps
 mbd_status mbd_energy_forces(mbd_system *sys, int32_t n_probes, int32_t n_steps, uint64_t seed,
                              double *energy, double *forces_dev);
 
+/* ---- choice of the Ewald splitting, cutoffs and mesh (host only) ----
+ * The paper's convergence study of Delta_11 against the mesh (Numerical
+ * results section) finds the SPME error set by the density of mesh points,
+ * independently of the system, and takes 1.2 points per angstrom along each
+ * box dimension as its default.  MBD_DEFAULT_MESH_DENSITY is that density in
+ * points per bohr. */
+#define MBD_DEFAULT_MESH_DENSITY (1.2 / 1.8897261254578281)
+
+/* mesh[a] = the smallest 2^a 3^b 5^c >= max(points_per_bohr x |a_a|, 2 p),
+ * a_a the rows of cell (bohr).  points_per_bohr <= 0 selects
+ * MBD_DEFAULT_MESH_DENSITY.  MBD_ERR_INVALID_ARG for a degenerate cell, an odd
+ * or out-of-range spline order, or a mesh above 1000. */
+mbd_status mbd_mesh_for_density(const double cell[9], double points_per_bohr, int32_t spline_order,
+                                int32_t mesh[3]);
+
+/* Ewald splitting beta_E, cutoffs and mesh for a target relative accuracy
+ * `tol` (0 < tol < 1) of the generalized field E = T'^pbc d (relative L2
+ * error over all atoms and components, for dipoles of random directions).
+ * Reads desc->cell, n_atoms, r_vdw (host [N]), damp_beta, damp_d,
+ * spline_order, and desc->r_cut as an upper bound on the real-space cutoff
+ * (<= 0: 12 bohr); writes desc->ewald_beta, r_cut, damp_cut and mesh.  The
+ * error budget is split evenly over three terms, each from an estimate that
+ * was calibrated against a converged direct Ewald sum:
+ *   erfc truncation    2 exp(-(beta_E r_cut)^2)
+ *   damping correction 0.1 (1 - s(damp_cut)), s the Fermi damping of the
+ *                      largest vdW-radius pair
+ *   mesh               c_p (beta_E h)^p, h = plane spacing / K, c_4 = 0.4,
+ *                      c_p = 0.1 for p >= 6
+ * Cutoffs are at most 0.49 x the smallest plane spacing of the cell.
+ * *est_err (may be NULL) receives the estimated error of the written
+ * parameters.  Returns MBD_ERR_UNSUPPORTED (parameters still written) when the
+ * cell is too small for the damping correction to reach its share of tol. */
+mbd_status mbd_spme_params(mbd_system_desc *desc, double tol, double *est_err);
+
 /* ---- batches of independent systems ----
  * The probes of one system are independent of one another, and so are whole
  * systems: the paper's parallel scheme distributes independent stochastic

@@ -21,6 +21,8 @@ STATUS = {
 MBD_FP64, MBD_MIXED = 0, 1
 MBD_EIGEN_FP64, MBD_EIGEN_DF64 = 0, 1
 MBD_TERM_REAL, MBD_TERM_RECIP, MBD_TERM_SELF, MBD_TERM_ALL = 1, 2, 4, 7
+MBD_ERR_UNSUPPORTED = 7
+MBD_DEFAULT_MESH_DENSITY = 1.2 / 1.8897261254578281     # points per bohr (1.2 per angstrom)
 
 
 class SystemDesc(ctypes.Structure):
@@ -91,6 +93,8 @@ SIGNATURES = {
     "mbd_apply_C": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_lanczos_energy": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, PD, PD, PD]),
     "mbd_energy_forces": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, c_void_p]),
+    "mbd_mesh_for_density": (c_int, [POINTER(c_double), c_double, c_int32, POINTER(c_int32)]),
+    "mbd_spme_params": (c_int, [POINTER(SystemDesc), c_double, PD]),
     "mbd_create_batch": (c_int, [c_int32, POINTER(SystemDesc), c_void_p, POINTER(c_void_p)]),
     "mbd_destroy_batch": (None, [c_void_p]),
     "mbd_batch_lanczos_energy": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_uint64), PD, PD, POINTER(c_int32)]),

@@ -12,8 +12,8 @@ from ctypes import byref, c_double, c_int32, c_uint64, c_void_p
 import numpy as np
 import torch
 
-from ._abi import (MBD_EIGEN_DF64, MBD_EIGEN_FP64, MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES, BatchInfo, Info,
-                   Profile, SystemDesc, check, lib)
+from ._abi import (MBD_EIGEN_DF64, MBD_EIGEN_FP64, MBD_ERR_UNSUPPORTED, MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES,
+                   BatchInfo, Info, Profile, SystemDesc, check, lib)
 
 PRECISIONS = {"fp64": MBD_FP64, "mixed": MBD_MIXED}
 EIGEN = {"fp64": MBD_EIGEN_FP64, "df64": MBD_EIGEN_DF64}
@@ -238,6 +238,33 @@ class MBDBatch:
         where = "mbd_batch_lanczos_energy" + (f" (member {bad.value})" if bad.value >= 0 else "")
         check(code, where)
         return e, t
+
+
+def mesh_for_density(cell, points_per_bohr: float = 0.0, spline_order: int = 6) -> tuple:
+    """mbd_mesh_for_density: the smooth mesh at a density of points per bohr
+    along each cell vector (<= 0: the paper's 1.2 points per angstrom)."""
+    c = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).ravel())
+    out = (c_int32 * 3)()
+    check(lib().mbd_mesh_for_density(c.ctypes.data_as(ctypes.POINTER(c_double)), float(points_per_bohr),
+                                     int(spline_order), out), "mbd_mesh_for_density")
+    return tuple(int(k) for k in out)
+
+
+def spme_params(s, tol: float, spline_order: int | None = None, r_cut_max: float = 0.0) -> dict:
+    """mbd_spme_params for a workloads.System-like object: the Ewald splitting,
+    cutoffs and mesh for a target relative accuracy of the field; 'ok' is False
+    when the cell is too small for the damping correction to reach it."""
+    kw = _workload_kw(s)
+    if spline_order is not None:
+        kw["spline_order"] = spline_order
+    kw["r_cut"] = r_cut_max
+    d, keep = _make_desc(s.cell, s.pos, s.alpha, s.omega, s.r_vdw, **kw)
+    est = c_double()
+    code = lib().mbd_spme_params(byref(d), float(tol), byref(est))
+    if code != MBD_ERR_UNSUPPORTED:
+        check(code, "mbd_spme_params")
+    return dict(ewald_beta=d.ewald_beta, r_cut=d.r_cut, damp_cut=d.damp_cut, mesh=tuple(int(k) for k in d.mesh),
+                spline_order=int(d.spline_order), est_err=est.value, ok=code != MBD_ERR_UNSUPPORTED)
 
 
 def generate_probes(seed: int, n_probes: int, dim: int, first: int = 0) -> torch.Tensor:

@@ -182,6 +182,35 @@ def water_system(n_mol: int, seed: int, mesh=None, box=None, **kw) -> System:
                   meta={"elements": elem}, **kw)
 
 
+# Diamond: conventional cubic cell (8 atoms), lattice constant 3.567 angstrom;
+# carbon free-atom polarizability, C6 and vdW radius of the Tkatchenko-Scheffler
+# reference set (12.0 bohr^3, 46.6 Ha bohr^6, 3.59 bohr), omega = 4 C6 / (3 alpha^2).
+ANGSTROM = 1.8897261254578281      # bohr
+DIAMOND_A = 3.567 * ANGSTROM
+CARBON_ALPHA, CARBON_C6, CARBON_RVDW = 12.0, 46.6, 3.59
+
+
+def diamond_system(n_cells: int = 4, seed: int = 0, jitter: float = 0.0, mesh=None, **kw) -> System:
+    """n_cells^3 conventional diamond cells (8 n_cells^3 atoms, 512 for n_cells = 4,
+    a 14.27 angstrom box), optionally with seeded Gaussian displacements."""
+    frac = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]], dtype=float)
+    frac = np.concatenate([frac, frac + 0.25])
+    cells = np.stack(np.meshgrid(*[np.arange(n_cells)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = ((cells[:, None, :] + frac[None, :, :]).reshape(-1, 3)) * DIAMOND_A
+    if jitter > 0.0:
+        pos = pos + np.random.Generator(np.random.PCG64(seed)).normal(scale=jitter, size=pos.shape)
+    box = n_cells * DIAMOND_A
+    n = pos.shape[0]
+    alpha = np.full(n, CARBON_ALPHA)
+    omega = np.full(n, 4.0 * CARBON_C6 / (3.0 * CARBON_ALPHA ** 2))
+    r_vdw = np.full(n, CARBON_RVDW)
+    if mesh is None:
+        k = smooth_size(box)
+        mesh = (k, k, k)
+    return System(name=kw.pop("name", f"diamond{n}"), cell=np.eye(3) * box, pos=np.mod(pos, box), alpha=alpha,
+                  omega=omega, r_vdw=r_vdw, mesh=tuple(mesh), **kw)
+
+
 # The five workloads.  Geometry seed 1000+c, probe seed 2307022780+c.
 def config(c: int, variant: str = "") -> System:
     probe_seed = 2307022780 + c
