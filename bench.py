@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 METRIC = "probe-matvecs/s and ms per MBD energy+forces at 1 GB300; frac of HBM roofline"
 UNIT = "probe-matvecs/s"
 WORKLOAD = 2        # the 3000-atom water box
+WORKLOADS = {"water3000": 2, "water24000": 3, "water100002": 5}
 
 
 def parse_args():
@@ -49,9 +50,14 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water3000", choices=["water3000", "batch64"],
-                    help="batch64: the 64 uneven random boxes (200-20000 atoms, 32 probes x 40 steps) run as "
-                         "one graph-replayed batch (energies)")
+    ap.add_argument("--workload", default="water3000", choices=list(WORKLOADS) + ["batch64"],
+                    help="water3000 (default, the bench line): 3000-atom water box, mesh 64^3, 64 x 50; "
+                         "water24000: 24000 atoms, mesh 128^3, 128 x 60; water100002: 100002 atoms, mesh 192^3, "
+                         "64 x 60; batch64: the 64 uneven random boxes (200-20000 atoms, 32 probes x 40 steps) "
+                         "run as one graph-replayed batch (energies)")
+    ap.add_argument("--cufft", action="store_true",
+                    help="also time the FFT convolution (forward 3D FFT, x G, inverse) with cuFFT (torch.fft) "
+                         "on the same complex mesh, next to the library's passes")
     ap.add_argument("--study", default="", choices=["", "delta11"],
                     help="delta11: Delta_11 against the mesh for the 14.2 angstrom water and diamond boxes, "
                          "and the parameters mbd_spme_params chooses (JSON lines)")
@@ -244,6 +250,44 @@ def cpu_baseline(seconds: float):
 
 
 # ---------------------------------------------------------------------------- our arm
+def cufft_comparison(mbd, s, precision, R, stream, reps=10):
+    """Device time of the FFT convolution of R probes on the workload's mesh:
+    the library's passes (mbd_convolve, stage profiler) against torch.fft
+    (cuFFT): forward 3D FFT, product with a real G, inverse, on the same complex
+    layout (two probes per complex value)."""
+    import numpy as np
+    import torch
+    K = tuple(s.mesh)
+    V = (R + 1) // 2
+    g = mbd.MBDSystem.from_workload(s, precision=precision, stream=stream)
+    q = torch.randn((R,) + K, dtype=torch.float64, device="cuda")
+    g.convolve(q)
+    g.profile_enable(True)
+    for _ in range(reps):
+        g.convolve(q)
+    prof = g.profile_read()
+    g.close()
+    del q
+    ours_ms = prof["fft"][1] / reps
+    cdt = torch.complex64 if precision == "mixed" else torch.complex128
+    x = torch.randn(K + (V,), dtype=cdt, device="cuda")
+    G = torch.rand(K + (1,), dtype=torch.float32 if precision == "mixed" else torch.float64, device="cuda")
+    ts = []
+    with torch.cuda.stream(stream):
+        for k in range(reps + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            y = torch.fft.ifftn(torch.fft.fftn(x, dim=(0, 1, 2)) * G, dim=(0, 1, 2))
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k >= 2:
+                ts.append(a.elapsed_time(b))
+    del x, y, G
+    torch.cuda.empty_cache()
+    return {"mesh": list(K), "probes": R, "ours_ms": ours_ms, "cufft_ms": float(np.median(ts)),
+            "note": "ours: 5 passes (k3, k2, k1 fused with G and its inverse, k2, k3); cuFFT: fftn, x G, ifftn"}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -258,7 +302,7 @@ def run_ours(args, world, rank, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2307_02278_gb300.parallel import reduce_estimates, shard_seed
-    s = config(WORKLOAD)
+    s = config(WORKLOADS[args.workload])
     R, m = s.n_probes, s.n_steps
     seed = shard_seed(s.probe_seed, rank, R)
     stream = torch.cuda.Stream()
@@ -392,8 +436,12 @@ def run_ours(args, world, rank, local):
             s64.close()
 
         cpu = None
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and args.workload == "water3000":
             cpu = cpu_baseline(args.cpu_seconds)
+
+        cufft = None
+        if args.cufft:
+            cufft = cufft_comparison(mbd, s, args.precision, R, stream)
 
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -417,6 +465,7 @@ def run_ours(args, world, rank, local):
             "e2e": e2e,
             "fp64_path": fp64,
             "cpu_baseline": cpu,
+            "cufft_comparison": cufft,
             "gpu_launches": int(prof["total_launches"]),
             "clocks": clocks,
             "wall_s_timed_region": wall,

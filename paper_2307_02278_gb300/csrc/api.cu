@@ -756,9 +756,10 @@ template <class T> mbd_status convolve_impl(mbd_system *s, int nvec, const doubl
     PrecData<T> &P = prec<T>(s);
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
     MBD_TRY(launch_mesh_in<T>(in, nvec, npts, ld, P.mesh.template as<T>(), s->stream));
-    MBD_TRY(launch_convolve<T>(s, P.mesh.template as<T>(), ld));
+    MBD_STAGE(s, MBD_STAGE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), ld));
     MBD_TRY(launch_mesh_out<T>(P.mesh.template as<T>(), nvec, npts, ld, out, s->stream));
     MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    prof_collect(s);
     return MBD_OK;
 }
 

@@ -24,8 +24,8 @@ template <class T> struct FFTArgs {
 // Compile-time passes for the smooth sizes listed below (fft_sizes_*.cu).
 // Return 1 when launched, 0 when the launch could not be configured, -1 when
 // there is no compile-time pass for the size or tile width asked for.
-//   a.W: the tile width; float passes exist for W = 32 (all passes) and
-//   W = 16 (unfused), double passes for W = 16.
+//   a.W: the tile width; float passes exist for W = 32 and 16, double
+//   passes for W = 16.
 template <class T> int launch_fft_ct_sized(const FFTArgs<T> &a, bool fused, unsigned grid, cudaStream_t st);
 //   W: the tile width of the fused spreading (float 32 or 16, double 16).
 template <class T>
@@ -338,13 +338,14 @@ template <class T, bool FUSED, int K, int W, int... RS> int launch_ct(const FFTA
     return 1;
 }
 
-// The passes of one size: float tiles of 32 (all passes) or 16 (unfused)
-// complex columns, double tiles of 16.
+// The passes of one size: float tiles of 32 or 16 complex columns, double
+// tiles of 16.
 template <class T, int K, int... RS> int ct_size(const FFTArgs<T> &a, bool fused, unsigned grid, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (a.W == 32) return fused ? launch_ct<T, true, K, 32, RS...>(a, grid, st)
                                     : launch_ct<T, false, K, 32, RS...>(a, grid, st);
-        if (a.W == 16 && !fused) return launch_ct<T, false, K, 16, RS...>(a, grid, st);
+        if (a.W == 16) return fused ? launch_ct<T, true, K, 16, RS...>(a, grid, st)
+                                    : launch_ct<T, false, K, 16, RS...>(a, grid, st);
     } else {
         if (a.W == 16) return fused ? launch_ct<T, true, K, 16, RS...>(a, grid, st)
                                     : launch_ct<T, false, K, 16, RS...>(a, grid, st);

@@ -544,10 +544,15 @@ template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, 
     return MBD_OK;
 }
 
+// FP32 passes and fused spreading over meshes longer than this use tiles of
+// 16 complex columns instead of 32: half the shared memory per block, twice
+// the resident blocks, which the long (latency-bound) spreading phase needs.
+constexpr int kWideTileMaxK = 96;
+
 // Tile width of the fused spreading + k3 pass for V complex probe-pair
 // columns: whole tiles only (float 32 or 16, double 16), 0 when none fits.
-int sf3_width(int V, int real_bytes) {
-    if (real_bytes == 4) return V % 32 == 0 ? 32 : (V % 16 == 0 ? 16 : 0);
+int sf3_width(int V, int real_bytes, int K3) {
+    if (real_bytes == 4) return (V % 32 == 0 && K3 <= kWideTileMaxK) ? 32 : (V % 16 == 0 ? 16 : 0);
     return V % 16 == 0 ? 16 : 0;
 }
 
@@ -591,13 +596,13 @@ int launch_sf3_sized(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, 
 // Spreading fused with the first forward FFT pass when the k3 size has a
 // compile-time pass and the probe-pair columns fill whole tiles.
 bool spread_fft3_supported(int K3, int ld, int real_bytes) {
-    return fft_ct_size(K3) && sf3_width(ld / 2, real_bytes) > 0;
+    return fft_ct_size(K3) && sf3_width(ld / 2, real_bytes, K3) > 0;
 }
 
 // Returns MBD_ERR_UNSUPPORTED (nothing launched) when spread_fft3_supported is false.
 template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *mesh, int R, int ld) {
     PrecData<T> &P = prec<T>(s);
-    const int W = sf3_width(ld / 2, (int)sizeof(T));
+    const int W = sf3_width(ld / 2, (int)sizeof(T), s->K[2]);
     if (W == 0) return MBD_ERR_UNSUPPORTED;
     using C = typename Cplx<T>::type;
     const int r = launch_sf3_sized<T>(s->K[2], W, d, mesh, R, ld, s->K[0], s->K[1], P.srow.template as<int>(),
@@ -630,10 +635,10 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bo
         a.W = inner < Wmax ? inner : Wmax;
         a.V = V;
         a.sign = sign;
-        // compile-time pass: float tiles of 32 complex columns (16 for the narrow
-        // unfused k3 pass), double tiles of 16; narrower rows are masked
+        // compile-time pass: float tiles of 32 complex columns (16 for narrow
+        // rows and for long meshes), double tiles of 16; narrower rows are masked
         FFTArgs<T> c = a;
-        c.W = (sizeof(T) == 4 && !fused && inner < 32) ? 16 : Wmax;
+        c.W = (sizeof(T) == 4 && (inner < 32 || a.K > kWideTileMaxK)) ? 16 : Wmax;
         const int r = launch_fft_ct_sized<T>(c, fused, (unsigned)((size_t)outer * ((inner + c.W - 1) / c.W)),
                                              s->stream);
         if (r == 0) {
