@@ -514,7 +514,9 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     z.ld = probe_ld(R);
     z.m = m;
     z.rows = rows;
-    z.nblk = std::max(1, std::min((rows + 15) / 16, 4096));
+    // prologue blocks per probe chunk: one per SM (fewer, fuller blocks keep the
+    // two-level norm reduction short), at least 16 rows each
+    z.nblk = std::max(1, std::min((rows + 15) / 16, std::max(1, s->num_sms)));
     const size_t ld = z.ld;
     const int nchunk = (z.ld + 31) / 32;
     MBD_TRY(s->Y.ensure(sizeof(double) * (size_t)m * rows * ld));
@@ -1113,6 +1115,13 @@ mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double ome
     s->N = (dim + 2) / 3;
     s->stream = nullptr;
     s->eigen_df64 = 0;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            s->num_sms = nsm;
+        cudaGetLastError();
+    }
     s->omega_sum = omega_sum;
     auto run = [&]() -> mbd_status {
         if (cudaMallocHost(&s->host_scal, 16 * sizeof(double)) != cudaSuccess) return MBD_ERR_OOM;
