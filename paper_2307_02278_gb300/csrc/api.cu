@@ -188,29 +188,29 @@ void wrap_positions(mbd_system *s, const double *pos) {
 mbd_status build_neighbors(mbd_system *s) {
     const double rmax = std::max(s->r_cut, s->damp_cut);
     const int N = s->N;
-    int nc[3], kk[3];
-    double width[3];
+    NeighborGrid ng;
+    ng.N = N;
     for (int a = 0; a < 3; ++a) {
         const double rn = std::sqrt(s->recip[3 * a] * s->recip[3 * a] + s->recip[3 * a + 1] * s->recip[3 * a + 1] +
                                     s->recip[3 * a + 2] * s->recip[3 * a + 2]);
-        width[a] = 1.0 / rn;
-        nc[a] = std::max(1, std::min(256, (int)std::floor(width[a] / rmax)));
-        kk[a] = (int)std::ceil(rmax * nc[a] / width[a] - 1e-12);
-        if (kk[a] > 120) return MBD_ERR_INVALID_ARG;
+        const double width = 1.0 / rn;
+        ng.nc[a] = std::max(1, std::min(256, (int)std::floor(width / rmax)));
+        ng.kk[a] = (int)std::ceil(rmax * ng.nc[a] / width - 1e-12);
+        if (ng.kk[a] > 120) return MBD_ERR_INVALID_ARG;
     }
-    const int ncell = nc[0] * nc[1] * nc[2];
-    std::vector<int> bin(N), cstart(ncell + 1, 0), catoms(N);
-    std::vector<int> cidx(3 * (size_t)N);
+    // cell binning on the host (O(N)), the pair search on the device
+    const int ncell = ng.nc[0] * ng.nc[1] * ng.nc[2];
+    std::vector<int> bin(N), cstart(ncell + 1, 0), catoms(N), cidx(3 * (size_t)N);
     for (int i = 0; i < N; ++i) {
         int b[3];
         for (int a = 0; a < 3; ++a) {
             double f = s->recip[3 * a] * s->pos[3 * i] + s->recip[3 * a + 1] * s->pos[3 * i + 1] +
                        s->recip[3 * a + 2] * s->pos[3 * i + 2];
             f -= std::floor(f);
-            b[a] = std::min(nc[a] - 1, std::max(0, (int)std::floor(f * nc[a])));
+            b[a] = std::min(ng.nc[a] - 1, std::max(0, (int)std::floor(f * ng.nc[a])));
             cidx[3 * i + a] = b[a];
         }
-        bin[i] = (b[0] * nc[1] + b[1]) * nc[2] + b[2];
+        bin[i] = (b[0] * ng.nc[1] + b[1]) * ng.nc[2] + b[2];
         cstart[bin[i] + 1]++;
     }
     for (int c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
@@ -218,59 +218,39 @@ mbd_status build_neighbors(mbd_system *s) {
         std::vector<int> fill(cstart.begin(), cstart.end() - 1);
         for (int i = 0; i < N; ++i) catoms[fill[bin[i]]++] = i;
     }
-    const double r2max = rmax * rmax;
-    s->h_row.assign(N + 1, 0);
-    s->h_col.clear();
-    s->h_shift.clear();
-    for (int i = 0; i < N; ++i) {
-        const double *pi = &s->pos[3 * i];
-        for (int o0 = -kk[0]; o0 <= kk[0]; ++o0) {
-            const int t0 = cidx[3 * i] + o0;
-            const int n0 = (int)std::floor((double)t0 / nc[0]);
-            const int b0 = t0 - n0 * nc[0];
-            for (int o1 = -kk[1]; o1 <= kk[1]; ++o1) {
-                const int t1 = cidx[3 * i + 1] + o1;
-                const int n1 = (int)std::floor((double)t1 / nc[1]);
-                const int b1 = t1 - n1 * nc[1];
-                for (int o2 = -kk[2]; o2 <= kk[2]; ++o2) {
-                    const int t2 = cidx[3 * i + 2] + o2;
-                    const int n2 = (int)std::floor((double)t2 / nc[2]);
-                    const int b2 = t2 - n2 * nc[2];
-                    const int c = (b0 * nc[1] + b1) * nc[2] + b2;
-                    double sh[3];
-                    for (int x = 0; x < 3; ++x)
-                        sh[x] = n0 * s->cell[x] + n1 * s->cell[3 + x] + n2 * s->cell[6 + x];
-                    for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
-                        const int j = catoms[q];
-                        const double *pj = &s->pos[3 * j];
-                        const double rx = pi[0] - pj[0] - sh[0], ry = pi[1] - pj[1] - sh[1],
-                                     rz = pi[2] - pj[2] - sh[2];
-                        const double r2 = rx * rx + ry * ry + rz * rz;
-                        if (r2 < r2max && r2 > 0.0) {
-                            if (std::abs(n0) > 127 || std::abs(n1) > 127 || std::abs(n2) > 127)
-                                return MBD_ERR_INVALID_ARG;
-                            s->h_col.push_back(j);
-                            s->h_shift.push_back((n0 + 128) | ((n1 + 128) << 8) | ((n2 + 128) << 16));
-                        }
-                    }
-                }
-            }
-        }
-        s->h_row[i + 1] = (int)s->h_col.size();
-        if (s->h_col.size() > (size_t)0x7fffffff - 1024) return MBD_ERR_INVALID_ARG;
-    }
-    s->nnz = (long long)s->h_col.size();
+    MBD_TRY(s->cell_start_d.ensure(sizeof(int) * (ncell + 1)));
+    MBD_TRY(s->cell_atoms_d.ensure(sizeof(int) * std::max(1, N)));
+    MBD_TRY(s->cell_idx_d.ensure(sizeof(int) * 3 * std::max<size_t>(1, N)));
+    MBD_TRY(s->nb_err_d.ensure(sizeof(int)));
     MBD_TRY(s->row_d.ensure(sizeof(int) * (N + 1)));
-    MBD_TRY(s->col_d.ensure(sizeof(int) * std::max<size_t>(1, s->h_col.size())));
-    MBD_TRY(s->shift_d.ensure(sizeof(int) * std::max<size_t>(1, s->h_col.size())));
-    MBD_CUDA_TRY(cudaMemcpyAsync(s->row_d.ptr, s->h_row.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice,
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->cell_start_d.ptr, cstart.data(), sizeof(int) * (ncell + 1),
+                                 cudaMemcpyHostToDevice, s->stream));
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->cell_atoms_d.ptr, catoms.data(), sizeof(int) * N, cudaMemcpyHostToDevice,
                                  s->stream));
-    if (s->nnz > 0) {
-        MBD_CUDA_TRY(cudaMemcpyAsync(s->col_d.ptr, s->h_col.data(), sizeof(int) * s->h_col.size(),
-                                     cudaMemcpyHostToDevice, s->stream));
-        MBD_CUDA_TRY(cudaMemcpyAsync(s->shift_d.ptr, s->h_shift.data(), sizeof(int) * s->h_shift.size(),
-                                     cudaMemcpyHostToDevice, s->stream));
-    }
+    MBD_CUDA_TRY(cudaMemcpyAsync(s->cell_idx_d.ptr, cidx.data(), sizeof(int) * 3 * N, cudaMemcpyHostToDevice,
+                                 s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->nb_err_d.ptr, 0, sizeof(int), s->stream));
+    ng.start = s->cell_start_d.as<int>();
+    ng.atoms = s->cell_atoms_d.as<int>();
+    ng.cidx = s->cell_idx_d.as<int>();
+    for (int k = 0; k < 9; ++k) ng.cell[k] = s->cell[k];
+    ng.r2max = rmax * rmax;
+    DevBuf cnt, bsum;
+    MBD_TRY(cnt.ensure(sizeof(int) * std::max(1, N)));
+    MBD_TRY(launch_neighbors(ng, s->pos_d.as<double>(), cnt.as<int>(), nullptr, nullptr, s->nb_err_d.as<int>(),
+                             false, s->stream));
+    MBD_TRY(launch_exclusive_scan(cnt.as<int>(), s->row_d.as<int>(), N, bsum, s->stream));
+    int head[2] = {0, 0};
+    MBD_CUDA_TRY(cudaMemcpyAsync(&head[0], s->row_d.as<int>() + N, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    MBD_CUDA_TRY(cudaMemcpyAsync(&head[1], s->nb_err_d.ptr, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (head[0] < 0 || head[1] != 0) return MBD_ERR_INVALID_ARG;
+    s->nnz = head[0];
+    MBD_TRY(s->col_d.ensure(sizeof(int) * std::max<size_t>(1, (size_t)s->nnz)));
+    MBD_TRY(s->shift_d.ensure(sizeof(int) * std::max<size_t>(1, (size_t)s->nnz)));
+    MBD_TRY(launch_neighbors(ng, s->pos_d.as<double>(), s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(),
+                             s->nb_err_d.as<int>(), true, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));   // cnt and bsum are freed on return
     return MBD_OK;
 }
 

@@ -489,39 +489,46 @@ Geom geom_of(const mbd_system *s) {
 
 }  // namespace
 
+mbd_status launch_exclusive_scan(const int *in, int *out, int n, DevBuf &bsum, cudaStream_t st) {
+    const int nb = (n + 4095) / 4096;
+    MBD_TRY(bsum.ensure(sizeof(int) * (size_t)std::max(1, nb)));
+    if (n > 0) {
+        k_scan_block<<<nb, 1024, 0, st>>>(in, out, bsum.as<int>(), n);
+        MBD_LAUNCH_CHECK();
+    }
+    k_scan_sums<<<1, 32, 0, st>>>(bsum.as<int>(), nb, out + n);
+    MBD_LAUNCH_CHECK();
+    if (n > 0) {
+        k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, bsum.as<int>(), n);
+        MBD_LAUNCH_CHECK();
+    }
+    return MBD_OK;
+}
+
 template <class T> mbd_status build_spread_matrix(mbd_system *s) {
     PrecData<T> &P = prec<T>(s);
     const Geom g = geom_of(s);
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
     if (npts >= 0x7fffffffULL) return MBD_ERR_UNSUPPORTED;
+    // every atom's stencil covers p^3 distinct points (K >= 2p), so the matrix
+    // has exactly p^3 N records
+    const size_t nnz = (size_t)s->p * s->p * s->p * (size_t)s->N;
+    if (nnz >= 0x7fffffffULL) return MBD_ERR_UNSUPPORTED;
     MBD_TRY(P.srow.ensure(sizeof(int) * (npts + 1)));
-    DevBuf cnt, bsum, total;
-    const int n = (int)npts;
-    const int nb = (n + 4095) / 4096;
+    MBD_TRY(P.srec.ensure(sizeof(SpreadRec<T>) * std::max<size_t>(1, nnz)));
+    DevBuf cnt, bsum;
     MBD_TRY(cnt.ensure(sizeof(int) * npts));
-    MBD_TRY(bsum.ensure(sizeof(int) * nb));
-    MBD_TRY(total.ensure(sizeof(int)));
     const int threads = 256;
     const unsigned blocks = (unsigned)((npts + threads - 1) / threads);
     k_spread_rows<T, false><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
                                                               s->dw64_d.as<double>(), cnt.as<int>(), nullptr);
     MBD_LAUNCH_CHECK();
-    k_scan_block<<<nb, 1024, 0, s->stream>>>(cnt.as<int>(), P.srow.template as<int>(), bsum.as<int>(), n);
-    MBD_LAUNCH_CHECK();
-    k_scan_sums<<<1, 32, 0, s->stream>>>(bsum.as<int>(), nb, P.srow.template as<int>() + n);
-    MBD_LAUNCH_CHECK();
-    k_scan_add<<<(n + 255) / 256, 256, 0, s->stream>>>(P.srow.template as<int>(), bsum.as<int>(), n);
-    MBD_LAUNCH_CHECK();
-    int nnz = 0;
-    MBD_CUDA_TRY(cudaMemcpyAsync(&nnz, P.srow.template as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    if (nnz < 0) return MBD_ERR_UNSUPPORTED;
-    MBD_TRY(P.srec.ensure(sizeof(SpreadRec<T>) * (size_t)(nnz > 0 ? nnz : 1)));
+    MBD_TRY(launch_exclusive_scan(cnt.as<int>(), P.srow.template as<int>(), (int)npts, bsum, s->stream));
     k_spread_rows<T, true><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
                                                              s->dw64_d.as<double>(), P.srow.template as<int>(),
                                                              P.srec.template as<SpreadRec<T>>());
     MBD_LAUNCH_CHECK();
-    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));   // cnt, bsum, total are freed on return
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));   // cnt and bsum are freed on return
     return MBD_OK;
 }
 

@@ -221,6 +221,58 @@ Geom make_geom(const mbd_system *s) {
     return g;
 }
 
+// Real-space neighbour list over a cell grid (cells of width >= rmax along
+// each reciprocal direction, kk cells searched each way).  A thread per atom i
+// visits the cells c = cidx(i) + o, o in [-kk, kk]^3, with their lattice
+// image n, and the atoms of each cell in order; FILL = false counts, FILL =
+// true writes (j, packed n).  The order is fixed, so the list is the same on
+// every run.  err bit 1: an image index beyond +-127.
+template <bool FILL>
+__global__ void k_neighbors(NeighborGrid ng, const double *__restrict__ pos, int *__restrict__ cnt_or_row,
+                            int *__restrict__ col, int *__restrict__ shift, int *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng.N) return;
+    const double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
+    int c = 0;
+    const int base = FILL ? cnt_or_row[i] : 0;
+    for (int o0 = -ng.kk[0]; o0 <= ng.kk[0]; ++o0) {
+        const int t0 = ng.cidx[3 * i] + o0;
+        const int n0 = t0 >= 0 ? t0 / ng.nc[0] : -((-t0 + ng.nc[0] - 1) / ng.nc[0]);
+        const int b0 = t0 - n0 * ng.nc[0];
+        for (int o1 = -ng.kk[1]; o1 <= ng.kk[1]; ++o1) {
+            const int t1 = ng.cidx[3 * i + 1] + o1;
+            const int n1 = t1 >= 0 ? t1 / ng.nc[1] : -((-t1 + ng.nc[1] - 1) / ng.nc[1]);
+            const int b1 = t1 - n1 * ng.nc[1];
+            for (int o2 = -ng.kk[2]; o2 <= ng.kk[2]; ++o2) {
+                const int t2 = ng.cidx[3 * i + 2] + o2;
+                const int n2 = t2 >= 0 ? t2 / ng.nc[2] : -((-t2 + ng.nc[2] - 1) / ng.nc[2]);
+                const int b2 = t2 - n2 * ng.nc[2];
+                const int cell = (b0 * ng.nc[1] + b1) * ng.nc[2] + b2;
+                const double sx = n0 * ng.cell[0] + n1 * ng.cell[3] + n2 * ng.cell[6];
+                const double sy = n0 * ng.cell[1] + n1 * ng.cell[4] + n2 * ng.cell[7];
+                const double sz = n0 * ng.cell[2] + n1 * ng.cell[5] + n2 * ng.cell[8];
+                const int q1 = ng.start[cell + 1];
+                for (int q = ng.start[cell]; q < q1; ++q) {
+                    const int j = ng.atoms[q];
+                    const double rx = px - pos[3 * j] - sx, ry = py - pos[3 * j + 1] - sy,
+                                 rz = pz - pos[3 * j + 2] - sz;
+                    const double r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 < ng.r2max && r2 > 0.0) {
+                        if (abs(n0) > 127 || abs(n1) > 127 || abs(n2) > 127) {
+                            if (!FILL) atomicOr(err, 1);
+                        } else if (FILL) {
+                            col[base + c] = j;
+                            shift[base + c] = (n0 + 128) | ((n1 + 128) << 8) | ((n2 + 128) << 16);
+                        }
+                        ++c;
+                    }
+                }
+            }
+        }
+    }
+    if (!FILL) cnt_or_row[i] = c;
+}
+
 template <class T> PrecData<T> &prec(mbd_system *s);
 template <> PrecData<double> &prec<double>(mbd_system *s) { return s->f64; }
 template <> PrecData<float> &prec<float>(mbd_system *s) { return s->f32; }
@@ -274,6 +326,18 @@ template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod
                                                                                    s->volume, P.G.template as<T>());
     MBD_LAUNCH_CHECK();
     MBD_CUDA_TRY(cudaStreamSynchronize(st));   // bm is freed on return
+    return MBD_OK;
+}
+
+mbd_status launch_neighbors(const NeighborGrid &ng, const double *pos, int *cnt_or_row, int *col, int *shift,
+                            int *err, bool fill, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((ng.N + 127) / 128);
+    if (ng.N == 0) return MBD_OK;
+    if (fill)
+        k_neighbors<true><<<blocks, 128, 0, st>>>(ng, pos, cnt_or_row, col, shift, err);
+    else
+        k_neighbors<false><<<blocks, 128, 0, st>>>(ng, pos, cnt_or_row, col, shift, err);
+    MBD_LAUNCH_CHECK();
     return MBD_OK;
 }
 

@@ -217,10 +217,10 @@ struct mbd_system {
     mbd::FFTDim fft[3];
     // host copies
     std::vector<double> pos, alpha, omega, rvdw;
-    std::vector<int> h_row, h_col, h_shift;
     // common device data
     mbd::DevBuf pos_d, g_d, w2_d, rvdw_d;            // [N][3], [N], [N], [N]
     mbd::DevBuf row_d, col_d, shift_d;              // CSR
+    mbd::DevBuf cell_start_d, cell_atoms_d, cell_idx_d, nb_err_d;   // neighbour-search cell grid
     mbd::DevBuf top_d;                              // [N][3]
     mbd::DevBuf w64_d, dw64_d;                      // [N][3][p] FP64 stencil weights (setup)
     mbd::DevBuf bin_start_d, bin_atoms_d, order_d;  // spread bins; field atom order
@@ -243,6 +243,18 @@ namespace mbd {
 
 // ---------------------------------------------------------------- launchers (kernels_*.cu)
 // setup
+struct NeighborGrid {
+    int N;
+    int nc[3], kk[3];       // cells per direction; cells searched each way
+    const int *start;       // [ncell + 1]
+    const int *atoms;       // [N] atoms by cell
+    const int *cidx;        // [N][3] cell coordinates of each atom
+    double cell[9];
+    double r2max;
+};
+mbd_status launch_neighbors(const NeighborGrid &ng, const double *pos, int *cnt_or_row, int *col, int *shift,
+                            int *err, bool fill, cudaStream_t st);
+mbd_status launch_exclusive_scan(const int *in, int *out, int n, DevBuf &bsum, cudaStream_t st);
 template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st);
 template <class T> mbd_status launch_splines(mbd_system *s, cudaStream_t st);
 template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod_host, cudaStream_t st);
