@@ -55,6 +55,8 @@ def parse_args():
                          "water24000: 24000 atoms, mesh 128^3, 128 x 60; water100002: 100002 atoms, mesh 192^3, "
                          "64 x 60; batch64: the 64 uneven random boxes (200-20000 atoms, 32 probes x 40 steps) "
                          "run as one graph-replayed batch (energies)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip mbd_autotune (launch choices by the built-in rules)")
     ap.add_argument("--cufft", action="store_true",
                     help="also time the FFT convolution (forward 3D FFT, x G, inverse) with cuFFT (torch.fft) "
                          "on the same complex mesh, next to the library's passes")
@@ -307,6 +309,7 @@ def run_ours(args, world, rank, local):
     seed = shard_seed(s.probe_seed, rank, R)
     stream = torch.cuda.Stream()
     sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, eigen_precision=args.eigen, stream=stream)
+    tuning = None if args.no_autotune else sysm.autotune(R)
     info = sysm.info()
     forces = torch.empty((s.n_atoms, 3), dtype=torch.float64, device="cuda")
     energy_t = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -454,6 +457,7 @@ def run_ours(args, world, rank, local):
                        "precision": args.precision, "eigensolve": args.eigen, "ewald_beta": s.ewald_beta,
                        "r_cut": s.r_cut,
                        "n_pairs": info["n_pairs"], "step": "mbd_energy_forces (energy + forces)",
+                       "autotune": tuning,
                        "l2": "flushed before every timed step (512 MB write, outside the events)",
                        "parallelism": f"probes sharded over {world} GPU(s)"},
             "ms_per_energy_forces": ms_per_step,

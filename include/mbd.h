@@ -210,6 +210,20 @@ typedef struct {
 } mbd_batch_info;
 mbd_status mbd_batch_get_info(const mbd_batch *batch, mbd_batch_info *info);
 
+/* ---- autotuning ----
+ * Times the candidate launch choices for this system at n_probes probes on the
+ * system's stream and keeps the fastest.  The candidates are the FP32 FFT tile
+ * width (32 or 16 complex columns), the tile width of the fused
+ * spreading + first FFT pass (32 or 16), and the field kernel's atoms per
+ * block (the occupancy-derived value, half and twice it, and four blocks per
+ * SM).  The choices hold for later calls with the same probe width and until
+ * the next mbd_autotune.  The tile widths do not change any result.  The
+ * atoms per block change the summation order of the a_k reductions (last-bit
+ * differences).  choices (host [4], may be NULL) receives the probe width,
+ * the atoms per block, the FFT tile and the spreading tile (0: not
+ * applicable). */
+mbd_status mbd_autotune(mbd_system *sys, int32_t n_probes, int32_t choices[4]);
+
 /* ---- stage-level entry points (per-stage checks and users of single stages) ---- */
 
 /* The normalised probes v_l (l = first..first+R-1) of the probe rule above,

@@ -568,7 +568,7 @@ mbd_status enqueue_lanczos(mbd_system *s, int R, int m, uint64_t seed, const uin
     fo.xin = nullptr;
     fo.lz = z.v;
     // the fused spread + k3 pass exists for the specialised sizes with whole probe-pair tiles
-    const bool fuse3 = spread_fft3_supported(s->K[2], z.ld, (int)sizeof(T));
+    const bool fuse3 = spread_fft3_supported(s, z.ld, (int)sizeof(T));
     for (int k = 0; k < m; ++k) {
         MBD_STAGE(s, MBD_STAGE_PROLOGUE, 1,
                   launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
@@ -663,7 +663,7 @@ mbd_status forces_impl(mbd_system *s, int R, int m, uint64_t seed, double *energ
     MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
               launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m,
                                         P.d.template as<T>(), ld2));
-    const bool fuse3 = spread_fft3_supported(s->K[2], ld2, (int)sizeof(T));
+    const bool fuse3 = spread_fft3_supported(s, ld2, (int)sizeof(T));
     if (fuse3) {
         MBD_STAGE(s, MBD_STAGE_FORCE_SPREAD, 1,
                   launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), ld2, ld2));
@@ -840,6 +840,103 @@ template <class T> mbd_status capture_batch(mbd_batch *b, int R, int m) {
     return MBD_OK;
 }
 
+// ---------------------------------------------------------------- autotuning
+// Time each candidate launch choice for probe width ld on the system's stream
+// (CUDA events, one untimed launch then three timed) and keep the fastest.
+template <class T> mbd_status autotune_impl(mbd_system *s, int R, int32_t *out) {
+    const int ld = probe_ld(R);
+    const size_t rows = 3 * (size_t)s->N;
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    PrecData<T> &P = prec<T>(s);
+    MBD_TRY(ensure_mesh<T>(s, ld));
+    MBD_TRY(s->L.ensure(sizeof(double) * rows * ld));
+    MBD_TRY(s->work2.ensure(sizeof(double) * rows * ld));
+    MBD_CUDA_TRY(cudaMemsetAsync(P.d.ptr, 0, sizeof(T) * rows * ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(P.mesh.ptr, 0, sizeof(T) * npts * ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->L.ptr, 0, sizeof(double) * rows * ld, s->stream));
+    s->tune_ld = ld;
+    s->tune_field_apb = s->tune_fft_w = s->tune_sf3_w = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MBD_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaGetLastError();
+        return MBD_ERR_CUDA;
+    }
+    mbd_status st = MBD_OK;
+    auto timed = [&](auto &&launch, float *ms) -> mbd_status {
+        MBD_TRY(launch());
+        MBD_CUDA_TRY(cudaEventRecord(e0, s->stream));
+        for (int r = 0; r < 3; ++r) MBD_TRY(launch());
+        MBD_CUDA_TRY(cudaEventRecord(e1, s->stream));
+        MBD_CUDA_TRY(cudaEventSynchronize(e1));
+        MBD_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+        return MBD_OK;
+    };
+    auto run = [&]() -> mbd_status {
+        float best = 0.0f, ms = 0.0f;
+        if (sizeof(T) == 4) {
+            // FFT tile width of every FP32 pass
+            int bw = 0;
+            for (int w : {32, 16}) {
+                s->tune_fft_w = w;
+                MBD_TRY(timed([&] { return launch_convolve<T>(s, P.mesh.template as<T>(), ld); }, &ms));
+                if (bw == 0 || ms < best) bw = w, best = ms;
+            }
+            s->tune_fft_w = bw;
+            // tile width of the fused spreading + k3 pass
+            if (fft_ct_size(s->K[2]) && (ld / 2) % 32 == 0) {
+                bw = 0;
+                for (int w : {32, 16}) {
+                    s->tune_sf3_w = w;
+                    MBD_TRY(timed([&] {
+                        return launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, ld);
+                    }, &ms));
+                    if (bw == 0 || ms < best) bw = w, best = ms;
+                }
+                s->tune_sf3_w = bw;
+            }
+        }
+        // atoms per block of the field kernel
+        const int a0 = field_apb(s, ld);
+        const int a4 = std::max(1, std::min(64, (s->N + 4 * s->num_sms - 1) / (4 * s->num_sms)));
+        std::vector<int> cand = {a0, std::max(1, a0 / 2), std::min(64, 2 * a0), a4};
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        FieldOut<T> fo;
+        fo.mode = kFieldApply;
+        fo.terms = MBD_TERM_ALL;
+        fo.out = s->work2.as<double>();
+        fo.xin = s->L.as<double>();
+        fo.k = 0;
+        std::memset(&fo.lz, 0, sizeof(fo.lz));
+        int ba = 0;
+        for (int apb : cand) {
+            s->tune_field_apb = apb;
+            MBD_TRY(timed([&] {
+                return launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, ld, fo);
+            }, &ms));
+            if (ba == 0 || ms < best) ba = apb, best = ms;
+        }
+        s->tune_field_apb = ba;
+        return MBD_OK;
+    };
+    st = run();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MBD_OK) {
+        s->tune_ld = s->tune_field_apb = s->tune_fft_w = s->tune_sf3_w = 0;
+        return st;
+    }
+    if (out) {
+        out[0] = ld;
+        out[1] = s->tune_field_apb;
+        out[2] = s->tune_fft_w;
+        out[3] = s->tune_sf3_w;
+    }
+    return MBD_OK;
+}
+
 mbd_status check_run_args(mbd_system *s, int R, int m, double *energy) {
     if (!s || !energy) return MBD_ERR_INVALID_ARG;
     if (R < 1 || R > (1 << 20) || m < 1 || m > kMaxSteps) return MBD_ERR_INVALID_ARG;
@@ -993,6 +1090,12 @@ mbd_status mbd_batch_get_info(const mbd_batch *b, mbd_batch_info *info) {
     info->graph_kernels = b->graph_kernels;
     info->total_atoms = b->total_atoms;
     return MBD_OK;
+}
+
+mbd_status mbd_autotune(mbd_system *s, int32_t n_probes, int32_t choices[4]) {
+    if (!s || n_probes < 1 || n_probes > (1 << 20)) return MBD_ERR_INVALID_ARG;
+    if (s->precision == MBD_FP64) return autotune_impl<double>(s, n_probes, choices);
+    return autotune_impl<float>(s, n_probes, choices);
 }
 
 mbd_status mbd_update_positions(mbd_system *s, const double *pos) {

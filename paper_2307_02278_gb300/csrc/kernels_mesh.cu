@@ -558,8 +558,11 @@ constexpr int kWideTileMaxK = 96;
 
 // Tile width of the fused spreading + k3 pass for V complex probe-pair
 // columns: whole tiles only (float 32 or 16, double 16), 0 when none fits.
-int sf3_width(int V, int real_bytes, int K3) {
-    if (real_bytes == 4) return (V % 32 == 0 && K3 <= kWideTileMaxK) ? 32 : (V % 16 == 0 ? 16 : 0);
+int sf3_width(const mbd_system *s, int V, int real_bytes) {
+    if (real_bytes == 4) {
+        if (s->tune_sf3_w != 0 && s->tune_ld == 2 * V && V % s->tune_sf3_w == 0) return s->tune_sf3_w;
+        return (V % 32 == 0 && s->K[2] <= kWideTileMaxK) ? 32 : (V % 16 == 0 ? 16 : 0);
+    }
     return V % 16 == 0 ? 16 : 0;
 }
 
@@ -602,14 +605,14 @@ int launch_sf3_sized(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, 
 
 // Spreading fused with the first forward FFT pass when the k3 size has a
 // compile-time pass and the probe-pair columns fill whole tiles.
-bool spread_fft3_supported(int K3, int ld, int real_bytes) {
-    return fft_ct_size(K3) && sf3_width(ld / 2, real_bytes, K3) > 0;
+bool spread_fft3_supported(const mbd_system *s, int ld, int real_bytes) {
+    return fft_ct_size(s->K[2]) && sf3_width(s, ld / 2, real_bytes) > 0;
 }
 
 // Returns MBD_ERR_UNSUPPORTED (nothing launched) when spread_fft3_supported is false.
 template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *mesh, int R, int ld) {
     PrecData<T> &P = prec<T>(s);
-    const int W = sf3_width(ld / 2, (int)sizeof(T), s->K[2]);
+    const int W = sf3_width(s, ld / 2, (int)sizeof(T));
     if (W == 0) return MBD_ERR_UNSUPPORTED;
     using C = typename Cplx<T>::type;
     const int r = launch_sf3_sized<T>(s->K[2], W, d, mesh, R, ld, s->K[0], s->K[1], P.srow.template as<int>(),
@@ -646,6 +649,7 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bo
         // rows and for long meshes), double tiles of 16; narrower rows are masked
         FFTArgs<T> c = a;
         c.W = (sizeof(T) == 4 && (inner < 32 || a.K > kWideTileMaxK)) ? 16 : Wmax;
+        if (sizeof(T) == 4 && s->tune_fft_w != 0 && s->tune_ld == ld) c.W = inner < 32 ? 16 : s->tune_fft_w;
         const int r = launch_fft_ct_sized<T>(c, fused, (unsigned)((size_t)outer * ((inner + c.W - 1) / c.W)),
                                              s->stream);
         if (r == 0) {
@@ -760,6 +764,7 @@ int field_resident_blocks(const mbd_system *s, int ld) {
 // resident-block capacity (blocks per SM x SMs, shared by the probe chunks),
 // with at most 64 atoms per block (more waves beyond that, for balance).
 int field_apb(const mbd_system *s, int ld) {
+    if (s->tune_field_apb > 0 && s->tune_ld == ld) return s->tune_field_apb;
     const int vec = field_vec(ld, s->precision == MBD_FP64 ? 8 : 4);
     const int ych = (ld + 32 * vec - 1) / (32 * vec);
     const long long per_wave = std::max(1, field_resident_blocks(s, ld) / ych);

@@ -212,6 +212,9 @@ struct mbd_system {
     int precision;
     int eigen_df64;     // tridiagonal eigensolve in double-float instead of FP64
     int num_sms = 1;    // multiprocessors of the device the system lives on
+    // launch choices made by mbd_autotune for probe width tune_ld (0: the
+    // built-in rules): field-kernel atoms per block, FP32 FFT and fused-spreading tiles
+    int tune_ld = 0, tune_field_apb = 0, tune_fft_w = 0, tune_sf3_w = 0;
     cudaStream_t stream;
     double omega_sum;
     mbd::FFTDim fft[3];
@@ -265,7 +268,8 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s);
 // in place; skip_first: the forward k3 pass was already done (launch_spread_fft3)
 template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bool skip_first = false);
 template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *mesh, int R, int ld);
-bool spread_fft3_supported(int K3, int ld, int real_bytes);
+bool spread_fft3_supported(const mbd_system *s, int ld, int real_bytes);
+bool fft_ct_size(int K);        // a compile-time FFT pass exists for this length
 enum FieldMode { kFieldOut = 0, kFieldApply = 1, kFieldLanczos = 2 };
 template <class T> struct FieldOut {
     int mode;

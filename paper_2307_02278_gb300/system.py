@@ -128,6 +128,12 @@ class MBDSystem:
         out["total_launches"] = int(p.total_launches)
         return out
 
+    def autotune(self, n_probes: int) -> dict:
+        """mbd_autotune: time the launch choices at n_probes probes, keep the fastest."""
+        out = (c_int32 * 4)()
+        check(lib().mbd_autotune(self._handle, int(n_probes), out), "mbd_autotune")
+        return dict(ld=out[0], field_atoms_per_block=out[1], fft_tile=out[2], spread_tile=out[3])
+
     def apply_C(self, x: torch.Tensor) -> torch.Tensor:
         """y = C x for x of shape [nvec, 3N] (or [3N])."""
         x = _cuda_f64(x, "x")
