@@ -210,6 +210,18 @@ typedef struct {
 } mbd_batch_info;
 mbd_status mbd_batch_get_info(const mbd_batch *batch, mbd_batch_info *info);
 
+/* ---- storage of the Lanczos basis ----
+ * The force estimator needs w_l = sum_k c_lk y_lk, which takes all m basis
+ * vectors of every probe.  MBD_BASIS_STORE (the default) keeps them,
+ * m x 3N x R FP64.  MBD_BASIS_RECOMPUTE keeps three and, in
+ * mbd_energy_forces, reruns the recurrence after the quadrature.  The rerun uses
+ * the same kernels in the same order, so it gives the same y_k, and it adds
+ * c_k y_k into w as each y_k is completed.  That costs about twice the
+ * Lanczos time, with memory for five vectors instead of m.  Energies are
+ * identical in both modes; forces agree to rounding of the sum for w. */
+enum { MBD_BASIS_STORE = 0, MBD_BASIS_RECOMPUTE = 1 };
+mbd_status mbd_set_basis_storage(mbd_system *sys, int32_t mode);
+
 /* ---- autotuning ----
  * Times the candidate launch choices for this system at n_probes probes on the
  * system's stream and keeps the fastest.  The candidates are the FP32 FFT tile

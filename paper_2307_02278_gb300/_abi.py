@@ -22,6 +22,7 @@ MBD_FP64, MBD_MIXED = 0, 1
 MBD_EIGEN_FP64, MBD_EIGEN_DF64 = 0, 1
 MBD_TERM_REAL, MBD_TERM_RECIP, MBD_TERM_SELF, MBD_TERM_ALL = 1, 2, 4, 7
 MBD_ERR_UNSUPPORTED = 7
+MBD_BASIS_STORE, MBD_BASIS_RECOMPUTE = 0, 1
 MBD_DEFAULT_MESH_DENSITY = 1.2 / 1.8897261254578281     # points per bohr (1.2 per angstrom)
 
 
@@ -93,6 +94,7 @@ SIGNATURES = {
     "mbd_apply_C": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_lanczos_energy": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, PD, PD, PD]),
     "mbd_energy_forces": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, c_void_p]),
+    "mbd_set_basis_storage": (c_int, [c_void_p, c_int32]),
     "mbd_autotune": (c_int, [c_void_p, c_int32, POINTER(c_int32)]),
     "mbd_mesh_for_density": (c_int, [POINTER(c_double), c_double, c_int32, POINTER(c_int32)]),
     "mbd_spme_params": (c_int, [POINTER(SystemDesc), c_double, PD]),

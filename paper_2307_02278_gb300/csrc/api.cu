@@ -499,7 +499,8 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     z.nblk = std::max(1, std::min((rows + 15) / 16, std::max(1, s->num_sms)));
     const size_t ld = z.ld;
     const int nchunk = (z.ld + 31) / 32;
-    MBD_TRY(s->Y.ensure(sizeof(double) * (size_t)m * rows * ld));
+    const int slots = s->basis_recompute ? std::min(3, m) : m;
+    MBD_TRY(s->Y.ensure(sizeof(double) * (size_t)slots * rows * ld));
     MBD_TRY(s->L.ensure(sizeof(double) * (size_t)rows * ld));
     MBD_TRY(s->a.ensure(sizeof(double) * (size_t)m * ld));
     MBD_TRY(s->b.ensure(sizeof(double) * (size_t)m * ld));
@@ -529,6 +530,9 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     z.v.partial = s->partial.as<double>();
     z.v.gpartial = s->gpartial.as<double>();
     z.v.counter = s->counter.as<unsigned>();
+    z.v.yslots = slots;
+    z.v.W = nullptr;
+    z.v.coef = nullptr;
     return MBD_OK;
 }
 
@@ -549,18 +553,13 @@ template <class T> mbd_status prepare_lanczos(mbd_system *s, int R, int m, Lz &z
     return MBD_OK;
 }
 
-// Algorithm 1 with Algorithm 2 per step: m Lanczos steps for all R probes, the
-// quadrature and the energy, enqueued on s->stream (kernels and memsets only,
-// so the sequence can be captured in a CUDA graph).  seed_dev, when set, is a
-// device word holding the seed (read by the first prologue).
+// The m steps of the recurrence (prologue, spreading, FFT convolution, field
+// kernel).  v0 (device [3N][ld], may be null) receives y_0 after the first step.
 template <class T>
-mbd_status enqueue_lanczos(mbd_system *s, int R, int m, uint64_t seed, const uint64_t *seed_dev, const Lz &z,
-                           bool full) {
+mbd_status enqueue_steps(mbd_system *s, int R, int m, uint64_t seed, const uint64_t *seed_dev, const Lz &z,
+                         double *v0) {
     const int rows = 3 * s->N;
     PrecData<T> &P = prec<T>(s);
-    MBD_CUDA_TRY(cudaMemsetAsync(s->a.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
-    MBD_CUDA_TRY(cudaMemsetAsync(s->b.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
-    MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
     FieldOut<T> fo;
     fo.mode = kFieldLanczos;
     fo.terms = MBD_TERM_ALL;
@@ -585,7 +584,25 @@ mbd_status enqueue_lanczos(mbd_system *s, int R, int m, uint64_t seed, const uin
         fo.k = k;
         MBD_STAGE(s, MBD_STAGE_FIELD, 1,
                   launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
+        if (k == 0 && v0)
+            MBD_CUDA_TRY(cudaMemcpyAsync(v0, z.v.Y, sizeof(double) * (size_t)rows * z.ld, cudaMemcpyDeviceToDevice,
+                                         s->stream));
     }
+    return MBD_OK;
+}
+
+// Algorithm 1 with Algorithm 2 per step: m Lanczos steps for all R probes, the
+// quadrature and the energy, enqueued on s->stream (kernels and memsets only,
+// so the sequence can be captured in a CUDA graph).  seed_dev, when set, is a
+// device word holding the seed (read by the first prologue).
+template <class T>
+mbd_status enqueue_lanczos(mbd_system *s, int R, int m, uint64_t seed, const uint64_t *seed_dev, const Lz &z,
+                           bool full) {
+    const int rows = 3 * s->N;
+    MBD_CUDA_TRY(cudaMemsetAsync(s->a.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->b.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
+    MBD_TRY(enqueue_steps<T>(s, R, m, seed, seed_dev, z, nullptr));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
               launch_tridiag(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(),
                              full ? s->work2.as<double>() : nullptr, s->status.as<int>(), s->stream,
@@ -660,9 +677,25 @@ mbd_status forces_impl(mbd_system *s, int R, int m, uint64_t seed, double *energ
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
     MBD_TRY(P.d.ensure(sizeof(T) * 3 * (size_t)s->N * std::max(ld2, z.ld)));
     MBD_TRY(P.mesh.ensure(sizeof(T) * npts * std::max(ld2, z.ld)));
-    MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
-              launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m,
-                                        P.d.template as<T>(), ld2));
+    if (s->basis_recompute) {
+        // rerun the recurrence (same kernels in the same order: the same y_k),
+        // adding c_k y_k into w as each y_k is completed
+        const size_t vbytes = sizeof(double) * 3 * (size_t)s->N * z.ld;
+        MBD_TRY(s->wacc.ensure(vbytes));
+        MBD_TRY(s->v0.ensure(vbytes));
+        MBD_CUDA_TRY(cudaMemsetAsync(s->wacc.ptr, 0, vbytes, s->stream));
+        Lz z2 = z;
+        z2.v.W = s->wacc.as<double>();
+        z2.v.coef = s->work2.as<double>();
+        MBD_TRY(enqueue_steps<T>(s, R, m, seed, nullptr, z2, s->v0.as<double>()));
+        MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
+                  launch_force_dipoles_w_t<T>(s, s->wacc.as<double>(), s->v0.as<double>(), R, z.ld,
+                                              P.d.template as<T>(), ld2));
+    } else {
+        MBD_STAGE(s, MBD_STAGE_FORCE_PREP, 1,
+                  launch_force_dipoles_t<T>(s, z.v.Y, s->work2.as<double>(), z.v.length, R, z.ld, m,
+                                            P.d.template as<T>(), ld2));
+    }
     const bool fuse3 = spread_fft3_supported(s, ld2, (int)sizeof(T));
     if (fuse3) {
         MBD_STAGE(s, MBD_STAGE_FORCE_SPREAD, 1,
@@ -1098,6 +1131,12 @@ mbd_status mbd_autotune(mbd_system *s, int32_t n_probes, int32_t choices[4]) {
     return autotune_impl<float>(s, n_probes, choices);
 }
 
+mbd_status mbd_set_basis_storage(mbd_system *s, int32_t mode) {
+    if (!s || (mode != MBD_BASIS_STORE && mode != MBD_BASIS_RECOMPUTE)) return MBD_ERR_INVALID_ARG;
+    s->basis_recompute = mode == MBD_BASIS_RECOMPUTE ? 1 : 0;
+    return MBD_OK;
+}
+
 mbd_status mbd_update_positions(mbd_system *s, const double *pos) {
     if (!s || !pos || !finite_all(pos, 3 * (size_t)s->N)) return MBD_ERR_INVALID_ARG;
     wrap_positions(s, pos);
@@ -1265,7 +1304,7 @@ mbd_status mbd_get_info(const mbd_system *s, mbd_info *info) {
     long long bytes = 0;
     const DevBuf *bufs[] = {&s->pos_d, &s->g_d, &s->w2_d, &s->rvdw_d, &s->row_d, &s->col_d, &s->shift_d,
                             &s->top_d, &s->bin_start_d, &s->bin_atoms_d, &s->order_d, &s->Y, &s->L, &s->a, &s->b,
-                            &s->invb, &s->length, &s->partial, &s->counter, &s->q, &s->scal, &s->status, &s->work,
+                            &s->invb, &s->length, &s->partial, &s->counter, &s->q, &s->scal, &s->status, &s->work, &s->wacc, &s->v0,
                             &s->work2, &s->f64.pairA, &s->f64.w, &s->f64.dw, &s->f64.d2w, &s->f64.G, &s->f64.d,
                             &s->f64.mesh, &s->f32.pairA, &s->f32.w, &s->f32.dw, &s->f32.d2w, &s->f32.G, &s->f32.d,
                             &s->f32.mesh};

@@ -32,6 +32,19 @@ __global__ void k_force_dipoles(int rows, const double *__restrict__ Y, const do
     dpq[(size_t)row * ld2 + 2 * r + 1] = T(gi * Y[(size_t)row * ld + r]);
 }
 
+// The same from w = sum_k c_k y_k accumulated during a rerun of the recurrence
+// (recomputed basis) and y_0 = v.
+template <class T>
+__global__ void k_force_dipoles_w(int rows, const double *__restrict__ w, const double *__restrict__ v,
+                                  const double *__restrict__ g, int R, int ld, T *__restrict__ dpq, int ld2) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * R) return;
+    const int row = (int)(idx / R), r = (int)(idx % R);
+    const double gi = g[row / 3];
+    dpq[(size_t)row * ld2 + 2 * r] = T(gi * w[(size_t)row * ld + r]);
+    dpq[(size_t)row * ld2 + 2 * r + 1] = T(gi * v[(size_t)row * ld + r]);
+}
+
 template <class T> struct ForceArgs {
     const T *dpq;        // [N][3][ld2] (p_l, q_l) interleaved
     const T *mesh;       // [K^3][ld2] (phi_p, phi_q) interleaved
@@ -168,6 +181,17 @@ mbd_status launch_force_dipoles_t(mbd_system *s, const double *Y, const double *
 }
 
 template <class T>
+mbd_status launch_force_dipoles_w_t(mbd_system *s, const double *w, const double *v, int R, int ld, T *dpq,
+                                    int ld2) {
+    const int rows = 3 * s->N;
+    const size_t n = (size_t)rows * R;
+    k_force_dipoles_w<T><<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(rows, w, v, s->g_d.as<double>(), R,
+                                                                            ld, dpq, ld2);
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+template <class T>
 mbd_status launch_force_gather_t(mbd_system *s, const T *dpq, const T *mesh, int R, int ld2, double scale,
                                  double *forces) {
     PrecData<T> &P = prec<T>(s);
@@ -202,6 +226,10 @@ template mbd_status launch_force_dipoles_t<double>(mbd_system *, const double *,
                                                    int, double *, int);
 template mbd_status launch_force_dipoles_t<float>(mbd_system *, const double *, const double *, const int *, int, int,
                                                   int, float *, int);
+template mbd_status launch_force_dipoles_w_t<double>(mbd_system *, const double *, const double *, int, int,
+                                                     double *, int);
+template mbd_status launch_force_dipoles_w_t<float>(mbd_system *, const double *, const double *, int, int, float *,
+                                                    int);
 template mbd_status launch_force_gather_t<double>(mbd_system *, const double *, const double *, int, int, double,
                                                   double *);
 template mbd_status launch_force_gather_t<float>(mbd_system *, const float *, const float *, int, int, double,

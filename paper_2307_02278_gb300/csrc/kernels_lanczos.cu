@@ -31,13 +31,13 @@ __global__ void __launch_bounds__(256) k_prologue(LanczosView lz, int k, int m, 
     const int r = blockIdx.y * 32 + lane;
     const bool valid = r < R;
     const size_t stride = (size_t)rows * ld;
-    double *Yk = lz.Y + (size_t)k * stride;
+    double *Yk = lz.Y + lz_slot(lz, k) * stride;
     double acc = 0.0;
     if (valid) {
         const double ak1 = k >= 1 ? lz.a[(size_t)(k - 1) * ld + r] : 0.0;
         const double bk2 = k >= 2 ? lz.b[(size_t)(k - 2) * ld + r] : 0.0;
-        const double *Yk1 = k >= 1 ? lz.Y + (size_t)(k - 1) * stride : nullptr;
-        const double *Yk2 = k >= 2 ? lz.Y + (size_t)(k - 2) * stride : nullptr;
+        const double *Yk1 = k >= 1 ? lz.Y + lz_slot(lz, k - 1) * stride : nullptr;
+        const double *Yk2 = k >= 2 ? lz.Y + lz_slot(lz, k - 2) * stride : nullptr;
         const double nrm0 = sqrt((double)rows);
         for (int row = blockIdx.x * 8 + ty; row < rows; row += gridDim.x * 8) {
             const size_t o = (size_t)row * ld + r;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_dense_matvec(const double *__restrict__
     const int r = blockIdx.y * 32 + lane;
     const int row = blockIdx.x * 8 + warp;
     if (row >= dim || r >= R) return;
-    const double *Yk = lz.Y + (size_t)k * dim * ld;
+    const double *Yk = lz.Y + lz_slot(lz, k) * dim * ld;
     double s = 0.0;
     for (int col = 0; col < dim; ++col) s += c[(size_t)row * dim + col] * Yk[(size_t)col * ld + r];
     lz.L[(size_t)row * ld + r] = s * lz.invb[r];
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_dense_epilogue(int dim, LanczosView lz,
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int r = blockIdx.y * 32 + lane;
     const bool valid = r < R;
-    double *Yk = lz.Y + (size_t)k * dim * ld;
+    double *Yk = lz.Y + lz_slot(lz, k) * dim * ld;
     double acc = 0.0;
     if (valid) {
         const double ib = lz.invb[r];

@@ -443,11 +443,12 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
                     a.o.out[o] = a.w2[i] * a.o.xin[o] + a.g_at[i] * E;
                 } else {
                     const double invb = a.o.lz.invb[r];
-                    double *Yk = a.o.lz.Y + (size_t)a.o.k * (size_t)(3 * a.g.N) * a.ld;
+                    double *Yk = a.o.lz.Y + lz_slot(a.o.lz, a.o.k) * (size_t)(3 * a.g.N) * a.ld;
                     const double y = Yk[o] * invb;
                     const double l = a.w2[i] * y + a.g_at[i] * E * invb;
                     Yk[o] = y;
                     a.o.lz.L[o] = l;
+                    if (a.o.lz.W) a.o.lz.W[o] += a.o.lz.coef[(size_t)a.o.k * a.ld + r] * y;
                     if (cp < (int)blockDim.x) part += y * l;
                     else pcarry[cp - blockDim.x] += y * l;   // thread cp - blockDim.x owns this slot
                 }

@@ -96,7 +96,9 @@ template <class T> struct PairView {
 };
 
 struct LanczosView {
-    double *Y;          // [m][3N][ld] basis (y* written by the prologue, y after the field kernel)
+    double *Y;          // [yslots][3N][ld] basis, y_k in slot k mod yslots (y* written by the
+                        // prologue, y after the field kernel); yslots = m, or 3 when the basis
+                        // is recomputed instead of stored
     double *L;          // [3N][ld] l_k = C y_k
     double *a;          // [m][ld]
     double *b;          // [m][ld]  b[k] couples y_k and y_{k+1}
@@ -106,7 +108,11 @@ struct LanczosView {
     double *gpartial;   // [ngroups][ld] group sums (two-level reduction)
     unsigned *counter;  // [nchunk][cstride] last-block counters (self-resetting)
     int cstride;        // counters per probe chunk (>= ngroups + 1)
+    int yslots;
+    double *W;          // [3N][ld] when set: the field kernel adds coef[k] y_k (recomputed basis)
+    const double *coef; // [m][ld] c = Delta^{-1/2} e_1, read with W
 };
+__host__ __device__ inline size_t lz_slot(const LanczosView &lz, int k) { return (size_t)(k % lz.yslots); }
 
 // Deterministic two-level reduction across the blocks of a grid row
 // (blockIdx.y = probe chunk).  Each block contributes bval[t] for the probes
@@ -215,6 +221,7 @@ struct mbd_system {
     // launch choices made by mbd_autotune for probe width tune_ld (0: the
     // built-in rules): field-kernel atoms per block, FP32 FFT and fused-spreading tiles
     int tune_ld = 0, tune_field_apb = 0, tune_fft_w = 0, tune_sf3_w = 0;
+    int basis_recompute = 0;    // MBD_BASIS_RECOMPUTE: three basis vectors kept, the forces rerun the recurrence
     cudaStream_t stream;
     double omega_sum;
     mbd::FFTDim fft[3];
@@ -234,6 +241,7 @@ struct mbd_system {
     mbd::PrecData<float> f32;
     // Lanczos workspace
     mbd::DevBuf Y, L, a, b, invb, length, partial, gpartial, counter, q, scal, status, work, work2;
+    mbd::DevBuf wacc, v0;       // recomputed basis: w = sum_k c_k y_k and y_0
     int counter_stride = 0;
     mbd::DevBuf forces_acc;
     mbd::Profiler prof;
@@ -307,6 +315,9 @@ template <class T> mbd_status launch_mesh_in(const double *in, int nvec, size_t 
                                              cudaStream_t st);
 
 // forces
+template <class T>
+mbd_status launch_force_dipoles_w_t(mbd_system *s, const double *w, const double *v, int R, int ld, T *dpq,
+                                    int ld2);
 template <class T>
 mbd_status launch_force_dipoles_t(mbd_system *s, const double *Y, const double *coef, const int *length, int R,
                                   int ld, int m, T *dpq, int ld2);

@@ -128,6 +128,12 @@ class MBDSystem:
         out["total_launches"] = int(p.total_launches)
         return out
 
+    def set_basis_storage(self, mode: str):
+        """mbd_set_basis_storage: "store" (all m Lanczos vectors) or "recompute"
+        (three kept; the forces rerun the recurrence)."""
+        code = {"store": 0, "recompute": 1}[mode]
+        check(lib().mbd_set_basis_storage(self._handle, code), "mbd_set_basis_storage")
+
     def autotune(self, n_probes: int) -> dict:
         """mbd_autotune: time the launch choices at n_probes probes, keep the fastest."""
         out = (c_int32 * 4)()
