@@ -222,15 +222,18 @@ Geom make_geom(const mbd_system *s) {
 }
 
 // Real-space neighbour list over a cell grid (cells of width >= rmax along
-// each reciprocal direction, kk cells searched each way).  A thread per atom i
+// each reciprocal direction, kk cells searched each way).  A warp per atom i
 // visits the cells c = cidx(i) + o, o in [-kk, kk]^3, with their lattice
-// image n, and the atoms of each cell in order; FILL = false counts, FILL =
+// image n; the lanes take the atoms of each cell 32 at a time, and a ballot
+// keeps the hits in cell order, then atom order.  FILL = false counts, FILL =
 // true writes (j, packed n).  The order is fixed, so the list is the same on
 // every run.  err bit 1: an image index beyond +-127.
 template <bool FILL>
-__global__ void k_neighbors(NeighborGrid ng, const double *__restrict__ pos, int *__restrict__ cnt_or_row,
-                            int *__restrict__ col, int *__restrict__ shift, int *__restrict__ err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_neighbors(NeighborGrid ng, const double *__restrict__ pos,
+                                                   int *__restrict__ cnt_or_row, int *__restrict__ col,
+                                                   int *__restrict__ shift, int *__restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (i >= ng.N) return;
     const double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
     int c = 0;
@@ -251,26 +254,32 @@ __global__ void k_neighbors(NeighborGrid ng, const double *__restrict__ pos, int
                 const double sx = n0 * ng.cell[0] + n1 * ng.cell[3] + n2 * ng.cell[6];
                 const double sy = n0 * ng.cell[1] + n1 * ng.cell[4] + n2 * ng.cell[7];
                 const double sz = n0 * ng.cell[2] + n1 * ng.cell[5] + n2 * ng.cell[8];
-                const int q1 = ng.start[cell + 1];
-                for (int q = ng.start[cell]; q < q1; ++q) {
-                    const int j = ng.atoms[q];
-                    const double rx = px - pos[3 * j] - sx, ry = py - pos[3 * j + 1] - sy,
-                                 rz = pz - pos[3 * j + 2] - sz;
-                    const double r2 = rx * rx + ry * ry + rz * rz;
-                    if (r2 < ng.r2max && r2 > 0.0) {
-                        if (abs(n0) > 127 || abs(n1) > 127 || abs(n2) > 127) {
-                            if (!FILL) atomicOr(err, 1);
-                        } else if (FILL) {
-                            col[base + c] = j;
-                            shift[base + c] = (n0 + 128) | ((n1 + 128) << 8) | ((n2 + 128) << 16);
-                        }
-                        ++c;
+                const bool far = abs(n0) > 127 || abs(n1) > 127 || abs(n2) > 127;
+                const int q0 = ng.start[cell], q1 = ng.start[cell + 1];
+                for (int qb = q0; qb < q1; qb += 32) {
+                    const int q = qb + lane;
+                    bool hit = false;
+                    int j = 0;
+                    if (q < q1) {
+                        j = ng.atoms[q];
+                        const double rx = px - pos[3 * j] - sx, ry = py - pos[3 * j + 1] - sy,
+                                     rz = pz - pos[3 * j + 2] - sz;
+                        const double r2 = rx * rx + ry * ry + rz * rz;
+                        hit = r2 < ng.r2max && r2 > 0.0;
                     }
+                    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                    if (hit && far && !FILL) atomicOr(err, 1);
+                    if (FILL && hit && !far) {
+                        const int at = base + c + __popc(bal & ((1u << lane) - 1u));
+                        col[at] = j;
+                        shift[at] = (n0 + 128) | ((n1 + 128) << 8) | ((n2 + 128) << 16);
+                    }
+                    c += __popc(bal);
                 }
             }
         }
     }
-    if (!FILL) cnt_or_row[i] = c;
+    if (!FILL && lane == 0) cnt_or_row[i] = c;
 }
 
 template <class T> PrecData<T> &prec(mbd_system *s);
@@ -331,7 +340,7 @@ template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod
 
 mbd_status launch_neighbors(const NeighborGrid &ng, const double *pos, int *cnt_or_row, int *col, int *shift,
                             int *err, bool fill, cudaStream_t st) {
-    const unsigned blocks = (unsigned)((ng.N + 127) / 128);
+    const unsigned blocks = (unsigned)((ng.N + 3) / 4);   // a warp per atom
     if (ng.N == 0) return MBD_OK;
     if (fill)
         k_neighbors<true><<<blocks, 128, 0, st>>>(ng, pos, cnt_or_row, col, shift, err);
