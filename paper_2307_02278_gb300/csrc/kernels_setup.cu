@@ -12,49 +12,61 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kSqrtPi = 1.77245385090551602730;
 
-// dA_ab / dr_c for the real-space pair tensor (FP64):
-//   erfc part  -B2 (delta_ab r_c + delta_ac r_b + delta_bc r_a) + B3 r_a r_b r_c
-//   damping    -d/dr_c [(1 - s) T_ab] with T_ab = delta_ab/r^3 - 3 r_a r_b / r^5
-__device__ void pair_tensor_grad(double rx, double ry, double rz, double rsum, double beta, double r_cut,
-                                      double damp_cut, double damp_beta, double damp_d, double out[18]) {
-    const double rv[3] = {rx, ry, rz};
-    const double r2 = rx * rx + ry * ry + rz * rz;
+// Radial coefficients of the real-space pair tensor A = c_id I - c_rr r r^T
+// (Eq. fld_ewald with the damping correction) and of its derivative,
+//   erfc part  c_id = B1, c_rr = B2 (Smith's B_n, (1/r) dB_n/dr = -B_{n+1})
+//   damping    c_id -= (1 - s)/r^3, c_rr -= 3 (1 - s)/r^5,
+// with cid_p = c_id'/r and crr_p = c_rr'/r.  FP64, with one reciprocal of r
+// in place of the divisions by powers of r.
+struct PairRadial {
+    double cid, crr, cid_p, crr_p;
+};
+__device__ __forceinline__ PairRadial pair_radial(double r2, double rsum, double beta, double r_cut,
+                                                  double damp_cut, double damp_beta, double damp_d) {
+    PairRadial pr{0.0, 0.0, 0.0, 0.0};
     const double rho = sqrt(r2);
-    // A = c_id I - c_rr r r^T with radial c_id, c_rr; dA_ab/dr_c =
-    //   (c_id'/rho) r_c delta_ab - (c_rr'/rho) r_c r_a r_b - c_rr (delta_ac r_b + delta_bc r_a)
-    double cid_p = 0.0, crr = 0.0, crr_p = 0.0;   // c_id'/rho, c_rr, c_rr'/rho
+    const double inv_rho = 1.0 / rho, inv_r2 = inv_rho * inv_rho;
     if (rho < r_cut) {
         const double e = exp(-beta * beta * r2);
-        const double b0 = erfc(beta * rho) / rho;
-        const double b1 = (b0 + 2.0 * beta / kSqrtPi * e) / r2;
-        const double b2 = (3.0 * b1 + 4.0 * beta * beta * beta / kSqrtPi * e) / r2;
-        const double b3 = (5.0 * b2 + 8.0 * beta * beta * beta * beta * beta / kSqrtPi * e) / r2;
-        // (1/r) dB_n/dr = -B_{n+1}
-        cid_p += -b2;
-        crr += b2;
-        crr_p += -b3;
+        const double b0 = erfc(beta * rho) * inv_rho;
+        const double b1 = (b0 + 2.0 * beta / kSqrtPi * e) * inv_r2;
+        const double b2 = (3.0 * b1 + 4.0 * beta * beta * beta / kSqrtPi * e) * inv_r2;
+        const double b3 = (5.0 * b2 + 8.0 * beta * beta * beta * beta * beta / kSqrtPi * e) * inv_r2;
+        pr.cid = b1;
+        pr.crr = b2;
+        pr.cid_p = -b2;
+        pr.crr_p = -b3;
     }
     if (rho < damp_cut) {
-        const double x = damp_d * (rho / (damp_beta * rsum) - 1.0);
+        const double inv_R = 1.0 / (damp_beta * rsum);
+        const double x = damp_d * (rho * inv_R - 1.0);
         const double oms = 1.0 / (1.0 + exp(x));          // 1 - s
         const double s = 1.0 - oms;
-        const double dsdr = damp_d / (damp_beta * rsum) * s * oms;
-        const double r3 = r2 * rho, r5 = r3 * r2;
-        // subtract (1-s) T:  c_id -= oms / r^3,  c_rr -= 3 oms / r^5
+        const double dsdr = damp_d * inv_R * s * oms;
+        const double inv_r3 = inv_r2 * inv_rho, inv_r5 = inv_r3 * inv_r2;
         // d/dr (oms / r^3) = -dsdr / r^3 - 3 oms / r^4 ;  d/dr (3 oms / r^5) = -3 dsdr / r^5 - 15 oms / r^6
-        cid_p -= (-dsdr / r3 - 3.0 * oms / (r3 * rho)) / rho;
-        crr -= 3.0 * oms / r5;
-        crr_p -= (-3.0 * dsdr / r5 - 15.0 * oms / (r5 * rho)) / rho;
+        pr.cid -= oms * inv_r3;
+        pr.crr -= 3.0 * oms * inv_r5;
+        pr.cid_p -= (-dsdr * inv_r3 - 3.0 * oms * inv_r3 * inv_rho) * inv_rho;
+        pr.crr_p -= (-3.0 * dsdr * inv_r5 - 15.0 * oms * inv_r5 * inv_rho) * inv_rho;
     }
+    return pr;
+}
+
+// dA_ab / dr_c = cid_p r_c delta_ab - crr_p r_c r_a r_b - c_rr (delta_ac r_b + delta_bc r_a),
+// (ab) over the 6 upper-triangle entries, c = x, y, z.
+__device__ __forceinline__ void pair_tensor_grad(double rx, double ry, double rz, const PairRadial &pr,
+                                                 double out[18]) {
+    const double rv[3] = {rx, ry, rz};
     int o = 0;
     for (int ab = 0; ab < 6; ++ab) {
         const int ia = ab < 3 ? 0 : (ab < 5 ? 1 : 2);
         const int ib = ab < 3 ? ab : (ab < 5 ? ab - 2 : 2);
         for (int c = 0; c < 3; ++c) {
-            double v = -crr_p * rv[c] * rv[ia] * rv[ib];
-            if (ia == ib) v += cid_p * rv[c];
-            if (ia == c) v -= crr * rv[ib];
-            if (ib == c) v -= crr * rv[ia];
+            double v = -pr.crr_p * rv[c] * rv[ia] * rv[ib];
+            if (ia == ib) v += pr.cid_p * rv[c];
+            if (ia == c) v -= pr.crr * rv[ib];
+            if (ib == c) v -= pr.crr * rv[ia];
             out[o++] = v;
         }
     }
@@ -62,8 +74,9 @@ __device__ void pair_tensor_grad(double rx, double ry, double rz, double rsum, d
 
 // Real-space pair tensor of E^dir with the damping correction (Eq. fld_ewald):
 //   A(r) = [|r| < r_cut] (B1 I - B2 r r^T) - [|r| < damp_cut] (1 - s(|r|)) T(r)
-// with Smith's erfc-screened B1, B2 and the bare T(r) = (r^2 I - 3 r r^T)/r^5.
-// Computed in FP64 from positions and the image shift, stored in T.
+// with Smith's erfc-screened B1, B2 and the bare T(r) = (r^2 I - 3 r r^T)/r^5,
+// and its derivative dA/dr (forces).  FP64 from positions and the image shift,
+// stored in T; a warp per atom, lanes over its neighbours.
 template <class T>
 __global__ void k_pair_tensors(int N, const double *__restrict__ pos, const double *__restrict__ rvdw,
                                const int *__restrict__ row, const int *__restrict__ col,
@@ -83,34 +96,18 @@ __global__ void k_pair_tensors(int N, const double *__restrict__ pos, const doub
         const double ry = yi - pos[3 * j + 1] - (n1 * g.cell[1] + n2 * g.cell[4] + n3 * g.cell[7]);
         const double rz = zi - pos[3 * j + 2] - (n1 * g.cell[2] + n2 * g.cell[5] + n3 * g.cell[8]);
         const double r2 = rx * rx + ry * ry + rz * rz;
-        const double rho = sqrt(r2);
-        double c_id = 0.0, c_rr = 0.0;   // A = c_id I - c_rr r r^T
-        if (rho < r_cut) {
-            const double e = exp(-beta * beta * r2);
-            const double b0 = erfc(beta * rho) / rho;
-            const double b1 = (b0 + 2.0 * beta / kSqrtPi * e) / r2;
-            const double b2 = (3.0 * b1 + 4.0 * beta * beta * beta / kSqrtPi * e) / r2;
-            c_id += b1;
-            c_rr += b2;
-        }
-        if (rho < damp_cut) {
-            const double rsum = rvdw[i] + rvdw[j];
-            const double one_minus_s = 1.0 / (1.0 + exp(damp_d * (rho / (damp_beta * rsum) - 1.0)));
-            const double r5 = r2 * r2 * rho;
-            c_id -= one_minus_s * r2 / r5;
-            c_rr -= one_minus_s * 3.0 / r5;
-        }
+        const PairRadial pr = pair_radial(r2, rvdw[i] + rvdw[j], beta, r_cut, damp_cut, damp_beta, damp_d);
         T *a = A + 6 * (size_t)nb;
-        a[0] = T(c_id - c_rr * rx * rx);
-        a[1] = T(-c_rr * rx * ry);
-        a[2] = T(-c_rr * rx * rz);
-        a[3] = T(c_id - c_rr * ry * ry);
-        a[4] = T(-c_rr * ry * rz);
-        a[5] = T(c_id - c_rr * rz * rz);
-        double g[18];
-        pair_tensor_grad(rx, ry, rz, rvdw[i] + rvdw[j], beta, r_cut, damp_cut, damp_beta, damp_d, g);
+        a[0] = T(pr.cid - pr.crr * rx * rx);
+        a[1] = T(-pr.crr * rx * ry);
+        a[2] = T(-pr.crr * rx * rz);
+        a[3] = T(pr.cid - pr.crr * ry * ry);
+        a[4] = T(-pr.crr * ry * rz);
+        a[5] = T(pr.cid - pr.crr * rz * rz);
+        double gr[18];
+        pair_tensor_grad(rx, ry, rz, pr, gr);
         T *ga = dA + 18 * (size_t)nb;
-        for (int c = 0; c < 18; ++c) ga[c] = T(g[c]);
+        for (int c = 0; c < 18; ++c) ga[c] = T(gr[c]);
     }
 }
 
