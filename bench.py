@@ -47,8 +47,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--eigen", default="fp64", choices=["fp64", "df64"],
-                    help="arithmetic of the tridiagonal eigensolve (fp64 default)")
+    ap.add_argument("--quadrature", default="chebyshev", choices=["chebyshev", "ql", "ql_df64"],
+                    help="evaluation of the per-probe Gauss quadrature (Chebyshev expansion with QL fallback, "
+                         "or the QL eigendecomposition in FP64 or double-float)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -311,7 +312,7 @@ def run_ours(args, world, rank, local):
     R, m = s.n_probes, s.n_steps
     seed = shard_seed(s.probe_seed, rank, R)
     stream = torch.cuda.Stream()
-    sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, eigen_precision=args.eigen, stream=stream)
+    sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, quadrature=args.quadrature, stream=stream)
     tuning = None if args.no_autotune else sysm.autotune(R)
     info = sysm.info()
     forces = torch.empty((s.n_atoms, 3), dtype=torch.float64, device="cuda")
@@ -465,7 +466,7 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh),
                        "spline_order": s.spline_order, "n_probes_per_gpu": R, "n_steps": m,
-                       "precision": args.precision, "eigensolve": args.eigen, "ewald_beta": s.ewald_beta,
+                       "precision": args.precision, "quadrature": args.quadrature, "ewald_beta": s.ewald_beta,
                        "r_cut": s.r_cut,
                        "n_pairs": info["n_pairs"], "step": "mbd_energy_forces (energy + forces)",
                        "autotune": tuning,
@@ -511,7 +512,7 @@ def run_batch(args, world, rank, local):
     seeds = np.array([s.probe_seed for s in systems], dtype=np.uint64)
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
-    batch = mbd.MBDBatch(systems, precision=args.precision, eigen_precision=args.eigen, stream=stream)
+    batch = mbd.MBDBatch(systems, precision=args.precision, quadrature=args.quadrature, stream=stream)
     setup_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     batch.lanczos_energy(R, m, seeds)            # records the graph
@@ -541,7 +542,7 @@ def run_batch(args, world, rank, local):
 
     # the same boxes one after another through mbd_lanczos_energy
     seq_ms = []
-    singles = [mbd.MBDSystem.from_workload(s, precision=args.precision, eigen_precision=args.eigen,
+    singles = [mbd.MBDSystem.from_workload(s, precision=args.precision, quadrature=args.quadrature,
                                            stream=stream) for s in systems]
     for s, g in zip(systems, singles):
         g.lanczos_energy(R, m, s.probe_seed)

@@ -60,12 +60,21 @@ typedef enum {
  * eigensolve and the trace sum are always FP64. */
 enum { MBD_FP64 = 0, MBD_MIXED = 1 /* FP32 operator, FP64 Lanczos */ };
 
-/* Arithmetic of the small tridiagonal eigensolve (Eq. tridiag2).  FP64 is the
- * default.  MBD_EIGEN_DF64 runs the same implicit-QL algorithm in double-float
- * arithmetic (pairs of FP32 numbers, 48-bit significand; quadrature values
- * agree with FP64 to about 1e-13 relative), several times faster on GPUs whose
- * FP64 issue rate is a small fraction of FP32. */
-enum { MBD_EIGEN_FP64 = 0, MBD_EIGEN_DF64 = 1 };
+/* Evaluation of each probe's Gauss quadrature (Eqs. tridiag2, sl3):
+ * q_l = sum_k U_1k^2 sqrt(theta_k) = e_1^T Delta^{1/2} e_1, and for the forces
+ * c = U diag(theta^{-1/2}) U^T e_1 = Delta^{-1/2} e_1.
+ *   MBD_QUAD_CHEBYSHEV (default, FP64): both from a Chebyshev expansion of
+ *     sqrt(x) and 1/sqrt(x) on an interval that contains the spectrum of Delta
+ *     (Gershgorin above, Sturm-count multisection below), applied to e_1 by the
+ *     three-term recurrence.  These are the same quantities as the
+ *     eigendecomposition route, to about 1e-13.  A probe whose Delta is too
+ *     ill-conditioned for 256 terms is done by QL.
+ *   MBD_QUAD_QL: the implicit-QL eigendecomposition of Delta (the paper's
+ *     route), FP64.
+ *   MBD_QUAD_QL_DF64: the same QL in double-float arithmetic (pairs of FP32
+ *     numbers, 48-bit significand; about 1e-13 from FP64).
+ * A Ritz value <= 0 gives MBD_ERR_NOT_POSITIVE_DEFINITE with every method. */
+enum { MBD_QUAD_CHEBYSHEV = 0, MBD_QUAD_QL_DF64 = 1, MBD_QUAD_QL = 2 };
 
 /* Field terms for mbd_field (bit mask). */
 enum { MBD_TERM_REAL = 1, MBD_TERM_RECIP = 2, MBD_TERM_SELF = 4, MBD_TERM_ALL = 7 };
@@ -95,7 +104,7 @@ typedef struct {
     int32_t mesh[3];          /* K_alpha: products of 2, 3, 5 only; 2p <= K_alpha <= 1000 */
     int32_t spline_order;     /* p: even, 4 <= p <= 10 */
     int32_t precision;        /* MBD_FP64 or MBD_MIXED */
-    int32_t eigen_precision;  /* MBD_EIGEN_FP64 (default) or MBD_EIGEN_DF64 */
+    int32_t quadrature;       /* MBD_QUAD_CHEBYSHEV (default), MBD_QUAD_QL or MBD_QUAD_QL_DF64 */
 } mbd_system_desc;
 
 /* Create a system: validate, upload, build the neighbour list, spline
@@ -257,9 +266,15 @@ mbd_status mbd_convolve(mbd_system *sys, int32_t nvec, const double *mesh_in_dev
 
 /* Gauss quadrature of a batch of tridiagonals (Eqs. tridiag2, sl3): host
  * a [R][m], b [R][m] (b[l][k] couples k and k+1; the entries from the first
- * zero on are ignored), q [R] out. */
+ * zero on are ignored), q [R] out; the default method (MBD_QUAD_CHEBYSHEV). */
 mbd_status mbd_tridiag_quadrature(int32_t n_probes, int32_t n_steps, const double *a_host,
                                   const double *b_host, double *q_host);
+
+/* The same with the method given (MBD_QUAD_*) and, if c_host is not NULL, the
+ * force coefficients c = Delta^{-1/2} e_1 as host [R][m] (zeros beyond each
+ * probe's length). */
+mbd_status mbd_tridiag_functions(int32_t n_probes, int32_t n_steps, const double *a_host, const double *b_host,
+                                 int32_t method, double *q_host, double *c_host);
 
 /* The quadrature of mbd_tridiag_quadrature for callers that cannot let the
  * library allocate device memory: callers whose device memory belongs to

@@ -19,7 +19,7 @@ STATUS = {
     7: "MBD_ERR_UNSUPPORTED", 8: "MBD_ERR_NO_DEVICE",
 }
 MBD_FP64, MBD_MIXED = 0, 1
-MBD_EIGEN_FP64, MBD_EIGEN_DF64 = 0, 1
+MBD_QUAD_CHEBYSHEV, MBD_QUAD_QL_DF64, MBD_QUAD_QL = 0, 1, 2
 MBD_TERM_REAL, MBD_TERM_RECIP, MBD_TERM_SELF, MBD_TERM_ALL = 1, 2, 4, 7
 MBD_ERR_UNSUPPORTED = 7
 MBD_BASIS_STORE, MBD_BASIS_RECOMPUTE = 0, 1
@@ -42,7 +42,7 @@ class SystemDesc(ctypes.Structure):
         ("mesh", c_int32 * 3),
         ("spline_order", c_int32),
         ("precision", c_int32),
-        ("eigen_precision", c_int32),
+        ("quadrature", c_int32),
     ]
 
 
@@ -107,6 +107,7 @@ SIGNATURES = {
     "mbd_spread": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_convolve": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_tridiag_quadrature": (c_int, [c_int32, c_int32, PD, PD, PD]),
+    "mbd_tridiag_functions": (c_int, [c_int32, c_int32, PD, PD, c_int32, PD, PD]),
     "mbd_tridiag_quadrature_noalloc": (c_int, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     "mbd_lanczos_energy_dense": (c_int, [c_int32, c_void_p, c_double, c_int32, c_int32, c_uint64, PD, PD, PD]),
     "mbd_get_info": (c_int, [c_void_p, POINTER(Info)]),

@@ -163,7 +163,8 @@ mbd_status validate(const mbd_system_desc *d) {
         if (d->mesh[a] < 2 * p || d->mesh[a] > 1000 || !factor_mesh(d->mesh[a], f)) return MBD_ERR_INVALID_ARG;
     }
     if (d->precision != MBD_FP64 && d->precision != MBD_MIXED) return MBD_ERR_INVALID_ARG;
-    if (d->eigen_precision != MBD_EIGEN_FP64 && d->eigen_precision != MBD_EIGEN_DF64) return MBD_ERR_INVALID_ARG;
+    if (d->quadrature != MBD_QUAD_CHEBYSHEV && d->quadrature != MBD_QUAD_QL && d->quadrature != MBD_QUAD_QL_DF64)
+        return MBD_ERR_INVALID_ARG;
     return MBD_OK;
 }
 
@@ -422,7 +423,7 @@ mbd_status create_impl(const mbd_system_desc *d, void *stream, mbd_system **out)
     s->damp_beta = d->damp_beta;
     s->damp_d = d->damp_d;
     s->precision = d->precision;
-    s->eigen_df64 = d->eigen_precision == MBD_EIGEN_DF64 ? 1 : 0;
+    s->quad_method = d->quadrature;
     s->stream = static_cast<cudaStream_t>(stream);
     {
         int dev = 0, nsm = 0;
@@ -521,6 +522,7 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     MBD_TRY(s->q.ensure(sizeof(double) * ld));
     MBD_TRY(s->scal.ensure(sizeof(double) * 16));
     MBD_TRY(s->status.ensure(sizeof(int) * 4));
+    MBD_TRY(s->qflag.ensure(sizeof(int) * ld));
     z.v.Y = s->Y.as<double>();
     z.v.L = s->L.as<double>();
     z.v.a = s->a.as<double>();
@@ -604,9 +606,9 @@ mbd_status enqueue_lanczos(mbd_system *s, int R, int m, uint64_t seed, const uin
     MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
     MBD_TRY(enqueue_steps<T>(s, R, m, seed, seed_dev, z, nullptr));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
-              launch_tridiag(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(),
-                             full ? s->work2.as<double>() : nullptr, s->status.as<int>(), s->stream,
-                             s->eigen_df64 != 0));
+              launch_quadrature(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(),
+                                full ? s->work2.as<double>() : nullptr, s->status.as<int>(), s->qflag.as<int>(),
+                                s->stream, s->quad_method));
     MBD_STAGE(s, MBD_STAGE_QUADRATURE, 1,
               launch_energy_reduce(s->q.as<double>(), R, rows, s->omega_sum, s->scal.as<double>(), s->stream));
     return MBD_OK;
@@ -1191,9 +1193,11 @@ mbd_status mbd_generate_probes(uint64_t seed, int32_t first, int32_t R, int32_t 
     return MBD_OK;
 }
 
-mbd_status mbd_tridiag_quadrature(int32_t R, int32_t m, const double *a_host, const double *b_host,
-                                  double *q_host) {
+mbd_status mbd_tridiag_functions(int32_t R, int32_t m, const double *a_host, const double *b_host, int32_t method,
+                                 double *q_host, double *c_host) {
     if (!a_host || !b_host || !q_host || R < 1 || m < 1 || m > kMaxSteps) return MBD_ERR_INVALID_ARG;
+    if (method != MBD_QUAD_CHEBYSHEV && method != MBD_QUAD_QL && method != MBD_QUAD_QL_DF64)
+        return MBD_ERR_INVALID_ARG;
     std::vector<double> a((size_t)m * R), b((size_t)m * R);
     std::vector<int> len(R);
     for (int r = 0; r < R; ++r) {
@@ -1209,23 +1213,36 @@ mbd_status mbd_tridiag_quadrature(int32_t R, int32_t m, const double *a_host, co
             b[(size_t)k * R + r] = b_host[(size_t)r * m + k];
         }
     }
-    DevBuf da, db, dl, dq, dst;
+    DevBuf da, db, dl, dq, dst, dflag, dc;
     MBD_TRY(da.ensure(sizeof(double) * a.size()));
     MBD_TRY(db.ensure(sizeof(double) * b.size()));
     MBD_TRY(dl.ensure(sizeof(int) * R));
     MBD_TRY(dq.ensure(sizeof(double) * R));
     MBD_TRY(dst.ensure(sizeof(int)));
+    MBD_TRY(dflag.ensure(sizeof(int) * R));
+    if (c_host) MBD_TRY(dc.ensure(sizeof(double) * a.size()));
     MBD_CUDA_TRY(cudaMemcpy(da.ptr, a.data(), sizeof(double) * a.size(), cudaMemcpyHostToDevice));
     MBD_CUDA_TRY(cudaMemcpy(db.ptr, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice));
     MBD_CUDA_TRY(cudaMemcpy(dl.ptr, len.data(), sizeof(int) * R, cudaMemcpyHostToDevice));
     MBD_CUDA_TRY(cudaMemset(dst.ptr, 0, sizeof(int)));
-    MBD_TRY(launch_tridiag(da.as<double>(), db.as<double>(), dl.as<int>(), R, R, m, dq.as<double>(), nullptr,
-                           dst.as<int>(), nullptr));
+    MBD_TRY(launch_quadrature(da.as<double>(), db.as<double>(), dl.as<int>(), R, R, m, dq.as<double>(),
+                              c_host ? dc.as<double>() : nullptr, dst.as<int>(), dflag.as<int>(), nullptr, method));
     int bits = 0;
     MBD_CUDA_TRY(cudaMemcpy(&bits, dst.ptr, sizeof(int), cudaMemcpyDeviceToHost));
     MBD_TRY(status_from_bits(bits));
     MBD_CUDA_TRY(cudaMemcpy(q_host, dq.ptr, sizeof(double) * R, cudaMemcpyDeviceToHost));
+    if (c_host) {
+        std::vector<double> c(a.size());
+        MBD_CUDA_TRY(cudaMemcpy(c.data(), dc.ptr, sizeof(double) * c.size(), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < R; ++r)
+            for (int k = 0; k < m; ++k) c_host[(size_t)r * m + k] = c[(size_t)k * R + r];
+    }
     return MBD_OK;
+}
+
+mbd_status mbd_tridiag_quadrature(int32_t R, int32_t m, const double *a_host, const double *b_host,
+                                  double *q_host) {
+    return mbd_tridiag_functions(R, m, a_host, b_host, MBD_QUAD_CHEBYSHEV, q_host, nullptr);
 }
 
 mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double omega_sum, int32_t R, int32_t m,
@@ -1236,7 +1253,7 @@ mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double ome
     if (!s) return MBD_ERR_OOM;
     s->N = (dim + 2) / 3;
     s->stream = nullptr;
-    s->eigen_df64 = 0;
+    s->quad_method = MBD_QUAD_CHEBYSHEV;
     {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -1260,8 +1277,8 @@ mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double ome
                                       z.nblk));
             MBD_TRY(launch_dense_step(c_dev, dim, z.v, k, R, z.ld, z.nblk, s->stream));
         }
-        MBD_TRY(launch_tridiag(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), nullptr,
-                               s->status.as<int>(), s->stream));
+        MBD_TRY(launch_quadrature(z.v.a, z.v.b, z.v.length, R, z.ld, m, s->q.as<double>(), nullptr,
+                                  s->status.as<int>(), s->qflag.as<int>(), s->stream, s->quad_method));
         MBD_TRY(launch_energy_reduce(s->q.as<double>(), R, dim, omega_sum, s->scal.as<double>(), s->stream));
         return fetch_results(s, z, energy, nullptr, q_host, ab_host);
     };

@@ -81,6 +81,226 @@ __global__ void __launch_bounds__(256) k_prologue(LanczosView lz, int k, int m, 
     }
 }
 
+// ---------------------------------------------------------------- Chebyshev quadrature
+// The Gauss quadrature of probe l (Eqs. tridiag2, sl3) is
+//   q_l = sum_k U_1k^2 sqrt(theta_k) = e_1^T Delta^{1/2} e_1,
+// and the force estimator's coefficients are c = U diag(theta^{-1/2}) U^T e_1 =
+// Delta^{-1/2} e_1.  Both are functions of Delta applied to e_1, so they need
+// no eigendecomposition: with [L, U] containing the spectrum of Delta,
+//   f(Delta) e_1 = sum_{j<N} c_j(f) T_j(X) e_1,  X = (Delta - mid I) / half,
+// with Chebyshev coefficients c_j(f) of f(mid + half xi) on [-1, 1] (error
+// decaying like rho^-N, rho = (sqrt(kappa) + 1) / (sqrt(kappa) - 1), kappa =
+// U / L).  One warp per probe; rows are spread over the lanes (row k in lane
+// k mod 32, register slot k / 32), so every step of the three-term recurrence
+// is one tridiagonal product with two shuffles.
+//   U: Gershgorin's upper bound.  L: two rounds of 32-way multisection with
+//   Sturm counts (the number of eigenvalues below x, from the signs of the
+//   characteristic polynomials of the leading blocks, rescaled to stay in
+//   range); L has count 0, so L <= theta_min.  A count > 0 at x = 0 means a
+//   non-positive Ritz value (status bit 1).
+// Probes with L <= 0 or kappa too large for kChebMax terms are flagged in
+// fallback[] for the QL kernel.  status bit 4: NaN/Inf in Delta.
+constexpr int kChebMax = 256;
+constexpr int kRowSlots = (kMaxSteps + 31) / 32;
+
+__device__ int sturm_count(const double *a, const double *b2, int n, double x) {
+    double pm = 1.0, p = a[0] - x;
+    int cnt = p < 0.0 ? 1 : 0;
+    for (int k = 1; k < n; ++k) {
+        double pn = (a[k] - x) * p - b2[k - 1] * pm;
+        if (pn == 0.0) pn = p < 0.0 ? 1e-300 : -1e-300;   // a zero is taken as a sign change
+        cnt += ((pn < 0.0) != (p < 0.0)) ? 1 : 0;
+        pm = p;
+        p = pn;
+        const double ap = fabs(p);
+        if (ap > 1e150) {
+            p *= 1e-150;
+            pm *= 1e-150;
+        } else if (ap < 1e-150 && fabs(pm) < 1e-150) {
+            p *= 1e150;
+            pm *= 1e150;
+        }
+    }
+    return cnt;
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(32) k_quad_cheb(const double *__restrict__ a, const double *__restrict__ b,
+                                                  const int *__restrict__ length, int R, int ld, int m,
+                                                  double *__restrict__ q, double *__restrict__ coef,
+                                                  int *__restrict__ status, int *__restrict__ fallback) {
+    __shared__ double sa[kMaxSteps], sb2[kMaxSteps], tab[4 * kChebMax], f1[kChebMax], f2[kChebMax];
+    __shared__ double c1[kChebMax], c2[kChebMax];
+    const int r = blockIdx.x, lane = threadIdx.x;
+    const int n = length ? length[r] : m;
+    // rows in registers: row k = lane + 32 t
+    double ar[kRowSlots], br[kRowSlots], bl[kRowSlots];
+    int finite = 1;
+    double glo = 1e300, ghi = -1e300;
+#pragma unroll
+    for (int t = 0; t < kRowSlots; ++t) {
+        const int k = lane + 32 * t;
+        ar[t] = br[t] = 0.0;
+        if (k < n) {
+            ar[t] = a[(size_t)k * ld + r];
+            br[t] = k < n - 1 ? b[(size_t)k * ld + r] : 0.0;
+            finite &= (isfinite(ar[t]) && isfinite(br[t])) ? 1 : 0;
+            sa[k] = ar[t];
+            sb2[k] = br[t] * br[t];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kRowSlots; ++t) {
+        // b_{k-1}: lane - 1 of the same slot, or lane 31 of the previous one
+        const double up = __shfl_up_sync(0xffffffffu, br[t], 1);
+        const double prev31 = __shfl_sync(0xffffffffu, t > 0 ? br[t > 0 ? t - 1 : 0] : 0.0, 31);
+        bl[t] = lane > 0 ? up : (t > 0 ? prev31 : 0.0);
+        const int k = lane + 32 * t;
+        if (k < n) {
+            const double rad = fabs(bl[t]) + fabs(br[t]);
+            glo = fmin(glo, ar[t] - rad);
+            ghi = fmax(ghi, ar[t] + rad);
+        }
+    }
+    finite = __all_sync(0xffffffffu, finite);
+    for (int off = 16; off > 0; off >>= 1) {
+        glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, off));
+        ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, off));
+    }
+    __syncwarp();
+    if (!finite) {
+        if (lane == 0) {
+            atomicOr(status, 4);
+            q[r] = 0.0;
+            fallback[r] = 0;
+        }
+        if (FULL)
+            for (int k = lane; k < m; k += 32) coef[(size_t)k * ld + r] = 0.0;
+        return;
+    }
+    // ---- spectrum bracket [L, U]
+    double lo = fmax(glo, 0.0), hi = ghi;
+    bool pd = true;
+    if (glo <= 0.0) {
+        int c0 = lane == 0 ? sturm_count(sa, sb2, n, 0.0) : 0;
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        pd = c0 == 0;
+    }
+    if (pd) {
+        for (int round = 0; round < 2; ++round) {
+            const double x = lo + (hi - lo) * (double)(lane + 1) / 32.0;
+            const int c = lane == 31 ? n : sturm_count(sa, sb2, n, x);   // hi: every eigenvalue below
+            const unsigned bal = __ballot_sync(0xffffffffu, c >= 1);
+            const int j = __ffs(bal) - 1;
+            const double nlo = j == 0 ? lo : lo + (hi - lo) * (double)j / 32.0;
+            const double nhi = lo + (hi - lo) * (double)(j + 1) / 32.0;
+            lo = nlo;
+            hi = nhi;
+        }
+    }
+    // widened by a relative 1e-13 so that the interval has a width even when a
+    // bound is an eigenvalue (a 1 x 1 Delta, a decoupled diagonal)
+    const double L = lo * (1.0 - 1e-13), U = ghi * (1.0 + 1e-13) + 1e-300;
+    int N = 0;
+    if (pd && L > 0.0) {
+        const double kap = U / L, sk = sqrt(kap);
+        const double lrho = log((sk + 1.0) / (sk - 1.0));
+        const double need = (log(1e17) + log(kap)) / lrho + 8.0;
+        N = 32;
+        while (N < need && N <= kChebMax) N *= 2;
+    }
+    if (!pd || N == 0 || N > kChebMax) {
+        // non-positive definite (bit 1, as the QL kernel), or the expansion cannot
+        // reach FP64 accuracy: QL takes the probe
+        if (lane == 0) {
+            if (!pd) atomicOr(status, 1);
+            q[r] = 0.0;
+            fallback[r] = pd ? 1 : 0;
+        }
+        if (FULL)
+            for (int k = lane; k < m; k += 32) coef[(size_t)k * ld + r] = 0.0;
+        return;
+    }
+    // ---- coefficients: c_j = (2/N) sum_i f(x_i) cos(pi j (i + 1/2) / N), x_i = mid + half cos(pi (i + 1/2) / N)
+    const double mid = 0.5 * (U + L), half = 0.5 * (U - L);
+    const int N4 = 4 * N;
+    for (int k = lane; k < N4; k += 32) tab[k] = cospi((double)k / (2.0 * N));
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) {
+        const double x = mid + half * tab[2 * i + 1];
+        const double sx = sqrt(x);
+        f1[i] = sx;
+        f2[i] = 1.0 / sx;
+    }
+    __syncwarp();
+    for (int j = lane; j < N; j += 32) {
+        double s1[4] = {0.0, 0.0, 0.0, 0.0}, s2[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < N; i += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double cv = tab[(j * (2 * (i + u) + 1)) & (N4 - 1)];
+                s1[u] += f1[i + u] * cv;
+                s2[u] += f2[i + u] * cv;
+            }
+        }
+        const double sc = (j == 0 ? 1.0 : 2.0) / N;     // c_0 / 2 for the j = 0 term
+        c1[j] = sc * ((s1[0] + s1[1]) + (s1[2] + s1[3]));
+        c2[j] = sc * ((s2[0] + s2[1]) + (s2[2] + s2[3]));
+    }
+    __syncwarp();
+    // ---- recurrence v_{j+1} = 2 X v_j - v_{j-1}, v_0 = e_1, accumulating sum c_j v_j
+    const double ih = 1.0 / half;
+    double am[kRowSlots], v0[kRowSlots], v1[kRowSlots], w[kRowSlots];
+#pragma unroll
+    for (int t = 0; t < kRowSlots; ++t) {
+        const int k = lane + 32 * t;
+        am[t] = k < n ? ar[t] - mid : 0.0;
+        v0[t] = k == 0 ? 1.0 : 0.0;
+        w[t] = c2[0] * v0[t];
+    }
+    double qa = c1[0];
+    // v1 = X e_1
+    auto matvec = [&](const double *v, double *y) {
+#pragma unroll
+        for (int t = 0; t < kRowSlots; ++t) {
+            const double left0 = __shfl_up_sync(0xffffffffu, v[t], 1);
+            const double l31 = __shfl_sync(0xffffffffu, v[t > 0 ? t - 1 : 0], 31);
+            const double right0 = __shfl_down_sync(0xffffffffu, v[t], 1);
+            const double r0 = __shfl_sync(0xffffffffu, v[t + 1 < kRowSlots ? t + 1 : t], 0);
+            const double left = lane > 0 ? left0 : (t > 0 ? l31 : 0.0);
+            const double right = lane < 31 ? right0 : (t + 1 < kRowSlots ? r0 : 0.0);
+            y[t] = (am[t] * v[t] + bl[t] * left + br[t] * right) * ih;
+        }
+    };
+    matvec(v0, v1);
+#pragma unroll
+    for (int t = 0; t < kRowSlots; ++t) w[t] += c2[1] * v1[t];
+    qa += c1[1] * __shfl_sync(0xffffffffu, v1[0], 0);
+    for (int j = 2; j < N; ++j) {
+        double y[kRowSlots];
+        matvec(v1, y);
+#pragma unroll
+        for (int t = 0; t < kRowSlots; ++t) {
+            const double vn = 2.0 * y[t] - v0[t];
+            v0[t] = v1[t];
+            v1[t] = vn;
+            w[t] += c2[j] * vn;
+        }
+        qa += c1[j] * __shfl_sync(0xffffffffu, v1[0], 0);
+    }
+    if (lane == 0) {
+        q[r] = qa;
+        fallback[r] = 0;
+    }
+    if (FULL) {
+#pragma unroll
+        for (int t = 0; t < kRowSlots; ++t) {
+            const int k = lane + 32 * t;
+            if (k < m) coef[(size_t)k * ld + r] = k < n ? w[t] : 0.0;
+        }
+    }
+}
+
 // Gauss quadrature of one probe's tridiagonal Delta (Eqs. tridiag2, sl3) by
 // implicit QL (ql.cuh), one block of two warps per probe.  Warp 0 runs the
 // sweeps (their scalar chain on lane 0) and records each sweep's rotations;
@@ -95,7 +315,8 @@ template <class S, bool FULL>
 __global__ void __launch_bounds__(64) k_tridiag(const double *__restrict__ a, const double *__restrict__ b,
                                                 const int *__restrict__ length, int R, int ld, int m,
                                                 double *__restrict__ q, double *__restrict__ coef,
-                                                int *__restrict__ status) {
+                                                int *__restrict__ status, const int *__restrict__ only) {
+    if (only != nullptr && only[blockIdx.x] == 0) return;   // this probe was done by the Chebyshev kernel
     extern __shared__ __align__(16) unsigned char sm_raw[];
     S *d = reinterpret_cast<S *>(sm_raw);
     S *e = d + m;
@@ -358,15 +579,15 @@ mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int 
 
 template <class S>
 mbd_status launch_tridiag_s(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
-                            double *coef, int *status, cudaStream_t st) {
+                            double *coef, int *status, cudaStream_t st, const int *only) {
     const bool full = coef != nullptr;
     const size_t smem = sizeof(S) * (size_t)(6 * m + (full ? m * (m + 1) : m + 1));
     if (full) {
         if (smem > 48 * 1024)
             MBD_CUDA_TRY(cudaFuncSetAttribute(k_tridiag<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_tridiag<S, true><<<R, 64, smem, st>>>(a, b, length, R, ld, m, q, coef, status);
+        k_tridiag<S, true><<<R, 64, smem, st>>>(a, b, length, R, ld, m, q, coef, status, only);
     } else {
-        k_tridiag<S, false><<<R, 64, smem, st>>>(a, b, length, R, ld, m, q, nullptr, status);
+        k_tridiag<S, false><<<R, 64, smem, st>>>(a, b, length, R, ld, m, q, nullptr, status, only);
     }
     MBD_LAUNCH_CHECK();
     return MBD_OK;
@@ -374,8 +595,21 @@ mbd_status launch_tridiag_s(const double *a, const double *b, const int *length,
 
 mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
                           double *coef, int *status, cudaStream_t st, bool df64) {
-    if (df64) return launch_tridiag_s<df>(a, b, length, R, ld, m, q, coef, status, st);
-    return launch_tridiag_s<double>(a, b, length, R, ld, m, q, coef, status, st);
+    if (df64) return launch_tridiag_s<df>(a, b, length, R, ld, m, q, coef, status, st, nullptr);
+    return launch_tridiag_s<double>(a, b, length, R, ld, m, q, coef, status, st, nullptr);
+}
+
+mbd_status launch_quadrature(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
+                             double *coef, int *status, int *fallback, cudaStream_t st, int method) {
+    if (method == MBD_QUAD_QL_DF64) return launch_tridiag_s<df>(a, b, length, R, ld, m, q, coef, status, st, nullptr);
+    if (method == MBD_QUAD_QL) return launch_tridiag_s<double>(a, b, length, R, ld, m, q, coef, status, st, nullptr);
+    if (coef)
+        k_quad_cheb<true><<<R, 32, 0, st>>>(a, b, length, R, ld, m, q, coef, status, fallback);
+    else
+        k_quad_cheb<false><<<R, 32, 0, st>>>(a, b, length, R, ld, m, q, coef, status, fallback);
+    MBD_LAUNCH_CHECK();
+    // probes whose spectrum the expansion cannot cover go through QL
+    return launch_tridiag_s<double>(a, b, length, R, ld, m, q, coef, status, st, fallback);
 }
 
 mbd_status launch_energy_reduce(const double *q, int R, int dim, double omega_sum, double *scal, cudaStream_t st) {

@@ -216,7 +216,7 @@ struct mbd_system {
     int K[3], p;
     double ewald_beta, r_cut, damp_cut, damp_beta, damp_d;
     int precision;
-    int eigen_df64;     // tridiagonal eigensolve in double-float instead of FP64
+    int quad_method;    // MBD_QUAD_*: Chebyshev quadrature (QL fallback) or QL
     int num_sms = 1;    // multiprocessors of the device the system lives on
     // launch choices made by mbd_autotune for probe width tune_ld (0: the
     // built-in rules): field-kernel atoms per block, FP32 FFT and fused-spreading tiles
@@ -241,6 +241,7 @@ struct mbd_system {
     mbd::PrecData<float> f32;
     // Lanczos workspace
     mbd::DevBuf Y, L, a, b, invb, length, partial, gpartial, counter, q, scal, status, work, work2;
+    mbd::DevBuf qflag;          // [ld] probes the Chebyshev quadrature hands to QL
     mbd::DevBuf wacc, v0;       // recomputed basis: w = sum_k c_k y_k and y_0
     int counter_stride = 0;
     mbd::DevBuf forces_acc;
@@ -297,6 +298,11 @@ mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int 
 // q [R] and, when coef != nullptr, c = Delta^{-1/2} e_1 as coef [m][ld]
 mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
                           double *coef, int *status, cudaStream_t st, bool df64 = false);
+// Quadrature of every probe's tridiagonal: MBD_QUAD_CHEBYSHEV (default) runs the
+// Chebyshev kernel and QL for the probes it flags in fallback [ld]; the QL methods
+// run QL for all.
+mbd_status launch_quadrature(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
+                             double *coef, int *status, int *fallback, cudaStream_t st, int method);
 mbd_status launch_energy_reduce(const double *q, int R, int dim, double omega_sum, double *scal, cudaStream_t st);
 mbd_status launch_probes(uint64_t seed, int first, int R, int dim, double *v, cudaStream_t st);
 mbd_status launch_dense_step(const double *c, int dim, const LanczosView &lz, int k, int R, int ld, int nblk,

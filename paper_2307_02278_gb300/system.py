@@ -12,11 +12,11 @@ from ctypes import byref, c_double, c_int32, c_uint64, c_void_p
 import numpy as np
 import torch
 
-from ._abi import (MBD_EIGEN_DF64, MBD_EIGEN_FP64, MBD_ERR_UNSUPPORTED, MBD_FP64, MBD_MIXED, MBD_TERM_ALL, STAGES,
-                   BatchInfo, Info, Profile, SystemDesc, check, lib)
+from ._abi import (MBD_ERR_UNSUPPORTED, MBD_FP64, MBD_MIXED, MBD_QUAD_CHEBYSHEV, MBD_QUAD_QL, MBD_QUAD_QL_DF64,
+                   MBD_TERM_ALL, STAGES, BatchInfo, Info, Profile, SystemDesc, check, lib)
 
 PRECISIONS = {"fp64": MBD_FP64, "mixed": MBD_MIXED}
-EIGEN = {"fp64": MBD_EIGEN_FP64, "df64": MBD_EIGEN_DF64}
+QUADRATURE = {"chebyshev": MBD_QUAD_CHEBYSHEV, "ql": MBD_QUAD_QL, "ql_df64": MBD_QUAD_QL_DF64}
 
 
 def _dptr(a: np.ndarray):
@@ -30,7 +30,7 @@ def _cuda_f64(t: torch.Tensor, name: str) -> torch.Tensor:
 
 
 def _make_desc(cell, pos, alpha, omega, r_vdw, *, damp_beta=0.83, damp_d=6.0, ewald_beta=0.35, r_cut=10.0,
-               damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64", eigen_precision="fp64"):
+               damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64", quadrature="chebyshev"):
     """An mbd_system_desc and the host arrays it points to (keep them alive while it is used)."""
     keep = [np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3),
             np.ascontiguousarray(alpha, dtype=np.float64), np.ascontiguousarray(omega, dtype=np.float64),
@@ -44,7 +44,7 @@ def _make_desc(cell, pos, alpha, omega, r_vdw, *, damp_beta=0.83, damp_d=6.0, ew
     d.mesh[:] = [int(k) for k in mesh]
     d.spline_order = int(spline_order)
     d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    d.eigen_precision = EIGEN[eigen_precision] if isinstance(eigen_precision, str) else int(eigen_precision)
+    d.quadrature = QUADRATURE[quadrature] if isinstance(quadrature, str) else int(quadrature)
     return d, keep
 
 
@@ -68,12 +68,12 @@ class MBDSystem:
 
     def __init__(self, cell, pos, alpha, omega, r_vdw, *, damp_beta=0.83, damp_d=6.0, ewald_beta=0.35,
                  r_cut=10.0, damp_cut=0.0, mesh=(32, 32, 32), spline_order=6, precision="fp64",
-                 eigen_precision="fp64", stream=None):
+                 quadrature="chebyshev", stream=None):
         self._handle = None
         d, self._keep = _make_desc(cell, pos, alpha, omega, r_vdw, damp_beta=damp_beta, damp_d=damp_d,
                                    ewald_beta=ewald_beta, r_cut=r_cut, damp_cut=damp_cut, mesh=mesh,
                                    spline_order=spline_order, precision=precision,
-                                   eigen_precision=eigen_precision)
+                                   quadrature=quadrature)
         self.n_atoms = d.n_atoms
         self._pos = self._keep[0]
         self.precision = precision
@@ -198,13 +198,13 @@ class MBDBatch:
     every member's Lanczos run is one branch of a CUDA graph recorded on the first
     call with a given (n_probes, n_steps) and replayed afterwards."""
 
-    def __init__(self, systems, precision="mixed", eigen_precision="fp64", stream=None):
+    def __init__(self, systems, precision="mixed", quadrature="chebyshev", stream=None):
         self._handle = None
         descs = (SystemDesc * len(systems))()
         self._keep = []
         for i, s in enumerate(systems):
             d, keep = _make_desc(s.cell, s.pos, s.alpha, s.omega, s.r_vdw, precision=precision,
-                                 eigen_precision=eigen_precision, **_workload_kw(s))
+                                 quadrature=quadrature, **_workload_kw(s))
             descs[i] = d
             self._keep.append(keep)
         self.n_sys = len(systems)
@@ -283,6 +283,17 @@ def generate_probes(seed: int, n_probes: int, dim: int, first: int = 0) -> torch
     v = torch.empty((n_probes, dim), dtype=torch.float64, device="cuda")
     check(lib().mbd_generate_probes(seed, first, n_probes, dim, v.data_ptr()), "mbd_generate_probes")
     return v
+
+
+def tridiag_functions(a: np.ndarray, b: np.ndarray, method: str = "chebyshev"):
+    """mbd_tridiag_functions: (q [R], c [R, m]) = (e1^T Delta^{1/2} e1, Delta^{-1/2} e1) per probe."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    q = np.zeros(a.shape[0])
+    c = np.zeros(a.shape)
+    check(lib().mbd_tridiag_functions(a.shape[0], a.shape[1], _dptr(a), _dptr(b), QUADRATURE[method], _dptr(q),
+                                      _dptr(c)), "mbd_tridiag_functions")
+    return q, c
 
 
 def tridiag_quadrature(a: np.ndarray, b: np.ndarray) -> np.ndarray:

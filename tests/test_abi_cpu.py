@@ -58,7 +58,7 @@ def _desc(**over):
     d.mesh[:] = list(over.get("mesh", (16, 16, 16)))
     d.spline_order = over.get("p", 6)
     d.precision = over.get("precision", 0)
-    d.eigen_precision = over.get("eigen", 0)
+    d.quadrature = over.get("eigen", 0)
     return d, keep
 
 
@@ -74,7 +74,7 @@ def _desc(**over):
     dict(p=12),
     dict(precision=3),
     dict(ewald_beta=0.0),
-    dict(eigen=2),
+    dict(eigen=3),
 ])
 def test_invalid_descriptors_rejected(libmbd, over):
     d, keep = _desc(**over)

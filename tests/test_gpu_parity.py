@@ -293,11 +293,11 @@ def test_fused_spread_fft_path(mbd, mesh, R, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_df64_eigensolver_option(mbd, precision):
-    """MBD_EIGEN_DF64 changes only the tridiagonal eigensolve: identical Lanczos
+    """MBD_QUAD_QL_DF64 changes only the quadrature: identical Lanczos
     coefficients, quadratures within 1e-12 and forces within 1e-11 of FP64."""
     s = _small()
     g64 = mbd.MBDSystem.from_workload(s, precision=precision)
-    gdf = mbd.MBDSystem.from_workload(s, precision=precision, eigen_precision="df64")
+    gdf = mbd.MBDSystem.from_workload(s, precision=precision, quadrature="ql_df64")
     e1, d1 = g64.lanczos_energy(16, 30, 5, details=True)
     e2, d2 = gdf.lanczos_energy(16, 30, 5, details=True)
     np.testing.assert_array_equal(d2["a"], d1["a"])
