@@ -138,22 +138,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def source_hash() -> str:
+def source_hash(files=None) -> str:
+    """Hash of the kernel sources (all of csrc, or the listed glob patterns)."""
+    import glob
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2307_02278_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    names = sorted(os.listdir(csrc)) if files is None else sorted(
+        {os.path.basename(f) for pat in files for f in glob.glob(os.path.join(csrc, pat))})
+    for fn in names:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
 
 
+# the sources each roofline stage's kernels are built from (a change to any
+# invalidates its recorded DRAM traffic)
+STAGE_SOURCES = {"fft": ["fft.cuh", "fft_sizes_*.cu", "kernels_mesh.cu", "mbd_internal.cuh"]}
+
+
 def dram_traffic(stage: str, workload: str):
     """Bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel sources (profiles/dram_traffic.txt: stage workload bytes hash)."""
+    current sources of the stage's kernels (profiles/dram_traffic.txt: stage
+    workload bytes hash)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    cur = source_hash()
+    cur = source_hash(STAGE_SOURCES.get(stage))
     with open(path) as f:
         for ln in f:
             p = ln.split()
