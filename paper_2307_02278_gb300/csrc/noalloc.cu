@@ -6,7 +6,8 @@
 // device-wide synchronisation that cudaMalloc/cudaFree imply.  This entry
 // point gives them the quadrature of mbd_tridiag_quadrature with caller-owned
 // device inputs and outputs; the little scratch it needs (the coefficients in
-// probe-innermost order, the Krylov lengths and a status word) lives in one
+// probe-innermost order, the Krylov lengths, a status word and the flags of
+// probes handed to QL) lives in one
 // file-scope device array that every GPU loading the library holds until the
 // process exits.
 #include "mbd_internal.cuh"
@@ -18,9 +19,9 @@ namespace {
 
 constexpr int kNoAllocMaxProbes = MBD_NOALLOC_MAX_PROBES;
 constexpr size_t kCoefBytes = sizeof(double) * (size_t)kMaxSteps * kNoAllocMaxProbes;   // 1 MiB
-constexpr size_t kScratchBytes = 2 * kCoefBytes + sizeof(int) * kNoAllocMaxProbes + 256;
+constexpr size_t kScratchBytes = 2 * kCoefBytes + 2 * sizeof(int) * kNoAllocMaxProbes + 256;
 
-// [a^T: m x R doubles][b^T: m x R doubles][length: R ints][status: int]
+// [a^T: m x R doubles][b^T: m x R doubles][length: R ints][status: int, padded][fallback: R ints]
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -78,10 +79,12 @@ extern "C" mbd_status mbd_tridiag_quadrature_noalloc(int32_t n_probes, int32_t n
     double *bt = reinterpret_cast<double *>(p + kCoefBytes);
     int *length = reinterpret_cast<int *>(p + 2 * kCoefBytes);
     int *status = reinterpret_cast<int *>(p + 2 * kCoefBytes + sizeof(int) * kNoAllocMaxProbes);
+    int *fallback = reinterpret_cast<int *>(p + 2 * kCoefBytes + sizeof(int) * kNoAllocMaxProbes + 256);
     k_noalloc_prepare<<<(n_probes + 127) / 128, 128, 0, st>>>(a_dev, b_dev, n_probes, n_steps, at, bt, length,
                                                              status);
     MBD_LAUNCH_CHECK();
-    MBD_TRY(launch_tridiag(at, bt, length, n_probes, n_probes, n_steps, q_dev, nullptr, status, st));
+    MBD_TRY(launch_quadrature(at, bt, length, n_probes, n_probes, n_steps, q_dev, nullptr, status, fallback, st,
+                              MBD_QUAD_CHEBYSHEV));
     int bits = 0;
     MBD_CUDA_TRY(cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     MBD_CUDA_TRY(cudaStreamSynchronize(st));
