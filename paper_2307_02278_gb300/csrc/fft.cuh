@@ -394,31 +394,42 @@ __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typ
             qb1 = row[pb + 1];
         }
         T ax = T(0), ay = T(0), bx = T(0), by = T(0);
+        // the next record of each row is loaded one iteration ahead, so that its
+        // latency overlaps the current record's dipole loads
+        SpreadRec<T> wa{}, wb{};
+        if (qa < qa1) wa = rec[qa];
+        if (qb < qb1) wb = rec[qb];
         while (qa < qa1 || qb < qb1) {
-            if (qa < qa1) {
-                const SpreadRec<T> w = rec[qa++];
+            const bool ha = qa < qa1, hb = qb < qb1;
+            SpreadRec<T> na = wa, nb = wb;
+            if (ha && qa + 1 < qa1) na = rec[qa + 1];
+            if (hb && qb + 1 < qb1) nb = rec[qb + 1];
+            if (ha) {
                 if (on) {
                     T x[2], y[2], z[2];
-                    const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
+                    const T *dj = d + (size_t)(3 * wa.atom) * ld + 2 * col;
                     vload<T, 2>(dj, x);
                     vload<T, 2>(dj + ld, y);
                     vload<T, 2>(dj + 2 * (size_t)ld, z);
-                    ax += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
-                    ay += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+                    ax += wa.w0 * x[0] + wa.w1 * y[0] + wa.w2 * z[0];
+                    ay += wa.w0 * x[1] + wa.w1 * y[1] + wa.w2 * z[1];
                 }
+                ++qa;
             }
-            if (qb < qb1) {
-                const SpreadRec<T> w = rec[qb++];
+            if (hb) {
                 if (on) {
                     T x[2], y[2], z[2];
-                    const T *dj = d + (size_t)(3 * w.atom) * ld + 2 * col;
+                    const T *dj = d + (size_t)(3 * wb.atom) * ld + 2 * col;
                     vload<T, 2>(dj, x);
                     vload<T, 2>(dj + ld, y);
                     vload<T, 2>(dj + 2 * (size_t)ld, z);
-                    bx += w.w0 * x[0] + w.w1 * y[0] + w.w2 * z[0];
-                    by += w.w0 * x[1] + w.w1 * y[1] + w.w2 * z[1];
+                    bx += wb.w0 * x[0] + wb.w1 * y[0] + wb.w2 * z[0];
+                    by += wb.w0 * x[1] + wb.w1 * y[1] + wb.w2 * z[1];
                 }
+                ++qb;
             }
+            wa = na;
+            wb = nb;
         }
         buf0[k3 * W + cl] = on ? C{ax * m0, ay * m1} : C{T(0), T(0)};
         if (kb < K) buf0[kb * W + cl] = on ? C{bx * m0, by * m1} : C{T(0), T(0)};
