@@ -443,7 +443,10 @@ def run_ours(args, world, rank, local):
         fp64 = None
         if args.precision == "mixed" and args.fp64_steps > 0:
             s64 = mbd.MBDSystem.from_workload(s, precision="fp64", stream=stream)
-            e64, _ = s64.energy_forces(R, m, seed)
+            e64, f64 = s64.energy_forces(R, m, seed)
+            f64 = f64.clone()
+            em, fm = sysm.energy_forces(R, m, seed)       # the mixed path on the same probes
+            force_rel = float((fm - f64).abs().max() / f64.abs().max())
             tt = []
             for k in range(args.fp64_steps):
                 flush.zero_()
@@ -456,7 +459,8 @@ def run_ours(args, world, rank, local):
                 tt.append(a.elapsed_time(b))
             ms64 = float(np.mean(tt))
             fp64 = {"value": R * m / (ms64 * 1e-3), "ms_per_step": ms64, "energy": e64,
-                    "mixed_energy_rel_diff": abs(energies[-1] - e64) / abs(e64),
+                    "mixed_energy_rel_diff": abs(em - e64) / abs(e64),
+                    "mixed_force_max_rel_diff": force_rel,
                     "speedup_mixed_over_fp64": ms64 / ms_per_step}
             s64.close()
 
