@@ -56,8 +56,8 @@ typedef enum {
 } mbd_status;
 
 /* Arithmetic of the operator C (spreading, FFT, influence function, gather,
- * real-space field).  The Lanczos vectors, dot products, the tridiagonal
- * eigensolve and the trace sum are always FP64. */
+ * real-space field).  The Lanczos vectors, dot products, the quadrature of
+ * the tridiagonal and the trace sum are always FP64. */
 enum { MBD_FP64 = 0, MBD_MIXED = 1 /* FP32 operator, FP64 Lanczos */ };
 
 /* Evaluation of each probe's Gauss quadrature (Eqs. tridiag2, sl3):
@@ -238,12 +238,21 @@ mbd_status mbd_set_basis_storage(mbd_system *sys, int32_t mode);
  * spreading + first FFT pass (32 or 16), and the field kernel's atoms per
  * block (the occupancy-derived value, half and twice it, and four blocks per
  * SM).  The choices hold for later calls with the same probe width and until
- * the next mbd_autotune.  The tile widths do not change any result.  The
+ * the next mbd_autotune or mbd_set_launch_choices.  The tile widths do not
+ * change any result.  The
  * atoms per block change the summation order of the a_k reductions (last-bit
  * differences).  choices (host [4], may be NULL) receives the probe width,
  * the atoms per block, the FFT tile and the spreading tile (0: not
  * applicable). */
 mbd_status mbd_autotune(mbd_system *sys, int32_t n_probes, int32_t choices[4]);
+
+/* Sets the launch choices directly, in the layout mbd_autotune returns, so
+ * that a saved result can be applied again without timing.  choices[0] = 0
+ * returns to the built-in rules; any other entry 0 keeps the built-in rule
+ * for that choice.  MBD_ERR_INVALID_ARG for a probe width that is not even and
+ * positive, atoms per block outside [0, 64], or tiles other than 0, 16 and 32
+ * (0 only for an FP64 system). */
+mbd_status mbd_set_launch_choices(mbd_system *sys, const int32_t choices[4]);
 
 /* ---- stage-level entry points (per-stage checks and users of single stages) ---- */
 
@@ -327,7 +336,7 @@ enum {
     MBD_STAGE_SPREAD = 1,       /* dipole array (Eq. dipolarr) */
     MBD_STAGE_FFT = 2,          /* forward FFT, influence function, inverse FFT (Eq. spme) */
     MBD_STAGE_FIELD = 3,        /* gather + real space + self + l_k, a_k (Eqs. spme, fld_ewald, lk3) */
-    MBD_STAGE_QUADRATURE = 4,   /* tridiagonal eigensolve, trace, energy (Eqs. tridiag2, sl4) */
+    MBD_STAGE_QUADRATURE = 4,   /* tridiagonal quadrature, trace, energy (Eqs. tridiag2, sl4) */
     MBD_STAGE_FORCE_PREP = 5,   /* Delta^{-1/2} e_1, w_l, (g.w_l, g.v_l) */
     MBD_STAGE_FORCE_SPREAD = 6,
     MBD_STAGE_FORCE_FFT = 7,

@@ -96,6 +96,7 @@ SIGNATURES = {
     "mbd_energy_forces": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, c_void_p]),
     "mbd_set_basis_storage": (c_int, [c_void_p, c_int32]),
     "mbd_autotune": (c_int, [c_void_p, c_int32, POINTER(c_int32)]),
+    "mbd_set_launch_choices": (c_int, [c_void_p, POINTER(c_int32)]),
     "mbd_mesh_for_density": (c_int, [POINTER(c_double), c_double, c_int32, POINTER(c_int32)]),
     "mbd_spme_params": (c_int, [POINTER(SystemDesc), c_double, PD]),
     "mbd_create_batch": (c_int, [c_int32, POINTER(SystemDesc), c_void_p, POINTER(c_void_p)]),

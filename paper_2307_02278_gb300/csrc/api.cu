@@ -1133,6 +1133,24 @@ mbd_status mbd_autotune(mbd_system *s, int32_t n_probes, int32_t choices[4]) {
     return autotune_impl<float>(s, n_probes, choices);
 }
 
+mbd_status mbd_set_launch_choices(mbd_system *s, const int32_t *c) {
+    if (!s || !c) return MBD_ERR_INVALID_ARG;
+    if (c[0] == 0) {
+        s->tune_ld = s->tune_field_apb = s->tune_fft_w = s->tune_sf3_w = 0;
+        return MBD_OK;
+    }
+    const bool fp32 = s->precision != MBD_FP64;
+    if (c[0] < 2 || c[0] % 2 != 0 || c[0] > (1 << 20) + 2) return MBD_ERR_INVALID_ARG;
+    if (c[1] < 0 || c[1] > 64) return MBD_ERR_INVALID_ARG;
+    if (c[2] != 0 && !(fp32 && (c[2] == 16 || c[2] == 32))) return MBD_ERR_INVALID_ARG;
+    if (c[3] != 0 && !(fp32 && (c[3] == 16 || c[3] == 32))) return MBD_ERR_INVALID_ARG;
+    s->tune_ld = c[0];
+    s->tune_field_apb = c[1];
+    s->tune_fft_w = c[2];
+    s->tune_sf3_w = c[3];
+    return MBD_OK;
+}
+
 mbd_status mbd_set_basis_storage(mbd_system *s, int32_t mode) {
     if (!s || (mode != MBD_BASIS_STORE && mode != MBD_BASIS_RECOMPUTE)) return MBD_ERR_INVALID_ARG;
     s->basis_recompute = mode == MBD_BASIS_RECOMPUTE ? 1 : 0;

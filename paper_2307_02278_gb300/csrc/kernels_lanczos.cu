@@ -593,12 +593,6 @@ mbd_status launch_tridiag_s(const double *a, const double *b, const int *length,
     return MBD_OK;
 }
 
-mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
-                          double *coef, int *status, cudaStream_t st, bool df64) {
-    if (df64) return launch_tridiag_s<df>(a, b, length, R, ld, m, q, coef, status, st, nullptr);
-    return launch_tridiag_s<double>(a, b, length, R, ld, m, q, coef, status, st, nullptr);
-}
-
 mbd_status launch_quadrature(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
                              double *coef, int *status, int *fallback, cudaStream_t st, int method) {
     if (method == MBD_QUAD_QL_DF64) return launch_tridiag_s<df>(a, b, length, R, ld, m, q, coef, status, st, nullptr);

@@ -218,8 +218,9 @@ struct mbd_system {
     int precision;
     int quad_method;    // MBD_QUAD_*: Chebyshev quadrature (QL fallback) or QL
     int num_sms = 1;    // multiprocessors of the device the system lives on
-    // launch choices made by mbd_autotune for probe width tune_ld (0: the
-    // built-in rules): field-kernel atoms per block, FP32 FFT and fused-spreading tiles
+    // launch choices made by mbd_autotune or mbd_set_launch_choices for probe
+    // width tune_ld (0: the built-in rules): field-kernel atoms per block, FP32
+    // FFT and fused-spreading tiles
     int tune_ld = 0, tune_field_apb = 0, tune_fft_w = 0, tune_sf3_w = 0;
     int basis_recompute = 0;    // MBD_BASIS_RECOMPUTE: three basis vectors kept, the forces rerun the recurrence
     cudaStream_t stream;
@@ -295,10 +296,8 @@ template <class T> mbd_status launch_field(mbd_system *s, const T *d, const T *m
 mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int m, uint64_t seed, int R, int ld,
                              int rows, const double *g, void *dout, int dtype_bytes, int nblk,
                              const uint64_t *seed_dev = nullptr);
-// q [R] and, when coef != nullptr, c = Delta^{-1/2} e_1 as coef [m][ld]
-mbd_status launch_tridiag(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,
-                          double *coef, int *status, cudaStream_t st, bool df64 = false);
-// Quadrature of every probe's tridiagonal: MBD_QUAD_CHEBYSHEV (default) runs the
+// Quadrature of every probe's tridiagonal, q [R] and, when coef != nullptr,
+// c = Delta^{-1/2} e_1 as coef [m][ld]: MBD_QUAD_CHEBYSHEV (default) runs the
 // Chebyshev kernel and QL for the probes it flags in fallback [ld]; the QL methods
 // run QL for all.
 mbd_status launch_quadrature(const double *a, const double *b, const int *length, int R, int ld, int m, double *q,

@@ -134,11 +134,22 @@ class MBDSystem:
         code = {"store": 0, "recompute": 1}[mode]
         check(lib().mbd_set_basis_storage(self._handle, code), "mbd_set_basis_storage")
 
+    _CHOICE_KEYS = ("ld", "field_atoms_per_block", "fft_tile", "spread_tile")
+
     def autotune(self, n_probes: int) -> dict:
         """mbd_autotune: time the launch choices at n_probes probes, keep the fastest."""
         out = (c_int32 * 4)()
         check(lib().mbd_autotune(self._handle, int(n_probes), out), "mbd_autotune")
-        return dict(ld=out[0], field_atoms_per_block=out[1], fft_tile=out[2], spread_tile=out[3])
+        return dict(zip(self._CHOICE_KEYS, list(out)))
+
+    def set_launch_choices(self, choices: dict | None) -> None:
+        """mbd_set_launch_choices: apply choices in the form autotune returns
+        (missing keys keep the built-in rule); None returns to the rules."""
+        c = (c_int32 * 4)()
+        if choices is not None:
+            for i, k in enumerate(self._CHOICE_KEYS):
+                c[i] = int(choices.get(k, 0))
+        check(lib().mbd_set_launch_choices(self._handle, c), "mbd_set_launch_choices")
 
     def apply_C(self, x: torch.Tensor) -> torch.Tensor:
         """y = C x for x of shape [nvec, 3N] (or [3N])."""
