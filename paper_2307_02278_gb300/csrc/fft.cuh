@@ -224,25 +224,41 @@ template <int K, int W, int... RS> constexpr int ct_threads() {
 // the global tile (IN_G, columns >= wc read as zero) or shared memory, and
 // writes the global tile (OUT_G, columns < wc only) or shared memory,
 // multiplying by G on the way out (MULG; G index row * gstride + (c0 + col) / V).
-template <class T, class C, int R, int K, int W, int NT, int NS, bool IN_G, bool OUT_G, bool MULG>
+// A thread takes CV adjacent columns of a row (CV = 2: float tiles, one
+// 16-byte access for both and one twiddle for both; the caller guarantees
+// whole column pairs, 16-byte alignment and an even V).
+template <class T, class C, int R, int K, int W, int NT, int CV, int NS, bool IN_G, bool OUT_G, bool MULG>
 __device__ __forceinline__ void ct_stage(const C *__restrict__ in_s, const C *__restrict__ in_g, C *__restrict__ out_s,
                                          C *__restrict__ out_g, size_t gs, int wc, const C *__restrict__ tw, int sign,
                                          const T *__restrict__ G, size_t gstride, int c0, int V) {
+    static_assert(CV == 1 || (CV == 2 && sizeof(T) == 4 && W % 2 == 0), "column pairs are float tiles");
     constexpr int nb = K / R;
     constexpr int step = K / (NS * R);
-    constexpr int total = nb * W;
+    constexpr int WG = W / CV;
+    constexpr int total = nb * WG;
 #pragma unroll
     for (int it = 0; it < (total + NT - 1) / NT; ++it) {
         const int idx = it * NT + (int)threadIdx.x;
         if (total % NT != 0 && idx >= total) break;
-        const int j = idx / W, col = idx % W;
-        C v[R];
+        const int j = idx / WG, col = (idx % WG) * CV;
+        C v[CV][R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            if (IN_G)
-                v[q] = col < wc ? in_g[(size_t)(j + q * nb) * gs + col] : C{T(0), T(0)};
-            else
-                v[q] = in_s[(j + q * nb) * W + col];
+            if constexpr (CV == 1) {
+                if (IN_G)
+                    v[0][q] = col < wc ? in_g[(size_t)(j + q * nb) * gs + col] : C{T(0), T(0)};
+                else
+                    v[0][q] = in_s[(j + q * nb) * W + col];
+            } else {
+                float4 x;
+                if (IN_G)
+                    x = col < wc ? *reinterpret_cast<const float4 *>(in_g + (size_t)(j + q * nb) * gs + col)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                else
+                    x = *reinterpret_cast<const float4 *>(in_s + (j + q * nb) * W + col);
+                v[0][q] = C{x.x, x.y};
+                v[1][q] = C{x.z, x.w};
+            }
         }
         const int jm = j % NS;
         if (NS > 1 && jm != 0) {
@@ -250,23 +266,37 @@ __device__ __forceinline__ void ct_stage(const C *__restrict__ in_s, const C *__
             for (int q = 1; q < R; ++q) {
                 C t = tw[q * jm * step];
                 if (sign > 0) t.y = -t.y;
-                v[q] = cmul(v[q], t);
+#pragma unroll
+                for (int u = 0; u < CV; ++u) v[u][q] = cmul(v[u][q], t);
             }
         }
-        dft<T, C, R>(v, sign);
+#pragma unroll
+        for (int u = 0; u < CV; ++u) dft<T, C, R>(v[u], sign);
         const int base = (j / NS) * NS * R + jm;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int row = base + q * NS;
             if (MULG && col < wc) {
                 const T gv = G[(size_t)row * gstride + (c0 + col) / V];
-                v[q].x *= gv;
-                v[q].y *= gv;
+#pragma unroll
+                for (int u = 0; u < CV; ++u) {
+                    v[u][q].x *= gv;
+                    v[u][q].y *= gv;
+                }
             }
-            if (OUT_G) {
-                if (col < wc) out_g[(size_t)row * gs + col] = v[q];
+            if constexpr (CV == 1) {
+                if (OUT_G) {
+                    if (col < wc) out_g[(size_t)row * gs + col] = v[0][q];
+                } else {
+                    out_s[row * W + col] = v[0][q];
+                }
             } else {
-                out_s[row * W + col] = v[q];
+                const float4 x = make_float4(v[0][q].x, v[0][q].y, v[1][q].x, v[1][q].y);
+                if (OUT_G) {
+                    if (col < wc) *reinterpret_cast<float4 *>(out_g + (size_t)row * gs + col) = x;
+                } else {
+                    *reinterpret_cast<float4 *>(out_s + row * W + col) = x;
+                }
             }
         }
     }
@@ -276,18 +306,18 @@ __device__ __forceinline__ void ct_stage(const C *__restrict__ in_s, const C *__
 // sin, intermediate results ping-pong between the shared buffers, the last
 // writes the global tile (OUT_G) or shared memory, multiplying by G (MULG).
 // Returns the shared buffer holding the result when it stays in shared memory.
-template <class T, class C, int K, int W, int NT, int NS, bool IN_G, bool OUT_G, bool MULG, int R, int... RS>
+template <class T, class C, int K, int W, int NT, int CV, int NS, bool IN_G, bool OUT_G, bool MULG, int R, int... RS>
 __device__ __forceinline__ C *ct_pipe(const C *gin, C *gout, size_t gs, int wc, C *sin, C *sout, const C *tw, int sign,
                                       const T *G, size_t gstride, int c0, int V) {
     constexpr bool last = sizeof...(RS) == 0;
-    ct_stage<T, C, R, K, W, NT, NS, IN_G, last && OUT_G, last && MULG>(sin, gin, sout, gout, gs, wc, tw, sign, G,
-                                                                       gstride, c0, V);
+    ct_stage<T, C, R, K, W, NT, CV, NS, IN_G, last && OUT_G, last && MULG>(sin, gin, sout, gout, gs, wc, tw, sign, G,
+                                                                           gstride, c0, V);
     if constexpr (last) {
         return sout;
     } else {
         __syncthreads();
-        return ct_pipe<T, C, K, W, NT, NS * R, false, OUT_G, MULG, RS...>(gin, gout, gs, wc, sout, sin, tw, sign, G,
-                                                                           gstride, c0, V);
+        return ct_pipe<T, C, K, W, NT, CV, NS * R, false, OUT_G, MULG, RS...>(gin, gout, gs, wc, sout, sin, tw, sign,
+                                                                               G, gstride, c0, V);
     }
 }
 
@@ -297,7 +327,7 @@ __device__ __forceinline__ C *ct_pipe(const C *gin, C *gout, size_t gs, int wc, 
 // and the last one stores straight from registers, so shared memory carries
 // only the exchanges between stages; the fused pass (forward, x G, inverse)
 // multiplies by G in the last forward stage.
-template <class T, bool FUSED, int K, int W, int NT, int... RS>
+template <class T, bool FUSED, int K, int W, int NT, int CV, int... RS>
 __global__ void __launch_bounds__(NT) k_fft_ct(FFTArgs<T> a) {
     using C = typename Cplx<T>::type;
     static_assert(sizeof...(RS) >= 2, "single-stage sizes would read and write the same global tile");
@@ -313,29 +343,40 @@ __global__ void __launch_bounds__(NT) k_fft_ct(FFTArgs<T> a) {
     C *base = a.data + outer * (size_t)K * a.inner + c0;
     const size_t gstride = (size_t)(a.inner / a.V);
     if (FUSED) {
-        C *res = ct_pipe<T, C, K, W, NT, 1, true, false, true, RS...>(base, base, a.inner, wc, buf0, buf1, tw, -1,
-                                                                       a.G, gstride, c0, a.V);
+        C *res = ct_pipe<T, C, K, W, NT, CV, 1, true, false, true, RS...>(base, base, a.inner, wc, buf0, buf1, tw,
+                                                                           -1, a.G, gstride, c0, a.V);
         __syncthreads();
         C *other = (res == buf0) ? buf1 : buf0;
-        ct_pipe<T, C, K, W, NT, 1, false, true, false, RS...>(base, base, a.inner, wc, res, other, tw, +1, a.G,
-                                                               gstride, c0, a.V);
+        ct_pipe<T, C, K, W, NT, CV, 1, false, true, false, RS...>(base, base, a.inner, wc, res, other, tw, +1, a.G,
+                                                                   gstride, c0, a.V);
     } else {
-        ct_pipe<T, C, K, W, NT, 1, true, true, false, RS...>(base, base, a.inner, wc, buf0, buf1, tw, a.sign, a.G,
-                                                              gstride, c0, a.V);
+        ct_pipe<T, C, K, W, NT, CV, 1, true, true, false, RS...>(base, base, a.inner, wc, buf0, buf1, tw, a.sign,
+                                                                  a.G, gstride, c0, a.V);
     }
 }
 
-template <class T, bool FUSED, int K, int W, int... RS> int launch_ct(const FFTArgs<T> &a, unsigned grid,
-                                                                      cudaStream_t st) {
+template <class T, bool FUSED, int K, int W, int CV, int... RS> int launch_ct_cv(const FFTArgs<T> &a, unsigned grid,
+                                                                              cudaStream_t st) {
     using C = typename Cplx<T>::type;
-    constexpr int NT = ct_threads<K, W, RS...>();
+    constexpr int NT = ct_threads<K, W / CV, RS...>();
     const size_t smem = sizeof(C) * (2 * (size_t)K * W + K);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_fft_ct<T, FUSED, K, W, NT, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_fft_ct<T, FUSED, K, W, NT, CV, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
-    k_fft_ct<T, FUSED, K, W, NT, RS...><<<grid, NT, smem, st>>>(a);
+    k_fft_ct<T, FUSED, K, W, NT, CV, RS...><<<grid, NT, smem, st>>>(a);
     return 1;
+}
+
+// Float tiles take column pairs when every tile is whole (inner a multiple of
+// W), so that the pairs are 16-byte aligned, and V is even, so that the two
+// columns of a pair share their G.
+template <class T, bool FUSED, int K, int W, int... RS> int launch_ct(const FFTArgs<T> &a, unsigned grid,
+                                                                      cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (a.inner % W == 0 && a.V % 2 == 0) return launch_ct_cv<T, FUSED, K, W, 2, RS...>(a, grid, st);
+    }
+    return launch_ct_cv<T, FUSED, K, W, 1, RS...>(a, grid, st);
 }
 
 // The passes of one size: float tiles of 32 or 16 complex columns, double
@@ -437,8 +478,8 @@ __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typ
     __syncthreads();
     const int wc = min(W, V - c0);
     C *base = mesh + pencil * (size_t)K * V + c0;
-    ct_pipe<T, C, K, W, NT, 1, false, true, false, RS...>(base, base, (size_t)V, wc, buf0, buf1, tw, -1,
-                                                           (const T *)nullptr, 0, c0, V);
+    ct_pipe<T, C, K, W, NT, 1, 1, false, true, false, RS...>(base, base, (size_t)V, wc, buf0, buf1, tw, -1,
+                                                              (const T *)nullptr, 0, c0, V);
 }
 
 template <class T, int K, int W, int... RS>
