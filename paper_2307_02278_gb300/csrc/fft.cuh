@@ -334,7 +334,9 @@ __global__ void __launch_bounds__(NT) k_fft_ct(FFTArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_ct[];
     C *buf0 = reinterpret_cast<C *>(smem_ct), *buf1 = buf0 + K * W;
     C *tw = buf1 + K * W;
-    for (int i = threadIdx.x; i < K; i += NT) tw[i] = a.tw[i];
+    pdl_launch_dependents();
+    for (int i = threadIdx.x; i < K; i += NT) tw[i] = a.tw[i];   // set up once per system
+    pdl_wait();
     __syncthreads();
     const int ncb = (a.inner + W - 1) / W;
     const size_t outer = blockIdx.x / ncb;
@@ -364,7 +366,7 @@ template <class T, bool FUSED, int K, int W, int CV, int... RS> int launch_ct_cv
         cudaFuncSetAttribute(k_fft_ct<T, FUSED, K, W, NT, CV, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
-    k_fft_ct<T, FUSED, K, W, NT, CV, RS...><<<grid, NT, smem, st>>>(a);
+    launch_pdl(k_fft_ct<T, FUSED, K, W, NT, CV, RS...>, dim3(grid), dim3(NT), smem, st, a);
     return 1;
 }
 
@@ -414,7 +416,9 @@ __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typ
     C *buf0 = reinterpret_cast<C *>(smem_sf);
     C *buf1 = buf0 + K * W;
     C *tw = buf1 + K * W;
-    for (int i = threadIdx.x; i < K; i += NT) tw[i] = twg[i];
+    pdl_launch_dependents();
+    for (int i = threadIdx.x; i < K; i += NT) tw[i] = twg[i];   // set up once per system
+    pdl_wait();
     const int V = ld / 2;
     const int ncb = (V + W - 1) / W;
     const size_t pencil = blockIdx.x / ncb;              // k1 * K2 + k2
@@ -494,8 +498,8 @@ int launch_sf3(const T *d, T *mesh, int R, int ld, int K1, int K2, const int *ro
         return 0;
     const int V = ld / 2;
     const unsigned grid = (unsigned)((size_t)K1 * K2 * ((V + W - 1) / W));
-    k_spread_fft3<T, K, W, NT, RS...><<<grid, NT, smem, st>>>(d, reinterpret_cast<C *>(mesh), R, ld, K2, row, rec,
-                                                              tw);
+    launch_pdl(k_spread_fft3<T, K, W, NT, RS...>, dim3(grid), dim3(NT), smem, st, d, reinterpret_cast<C *>(mesh), R,
+               ld, K2, row, rec, tw);
     return 1;
 }
 

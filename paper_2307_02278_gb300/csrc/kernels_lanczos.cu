@@ -26,6 +26,8 @@ template <class D>
 __global__ void __launch_bounds__(256) k_prologue(LanczosView lz, int k, int m, uint64_t seed,
                                                   const uint64_t *__restrict__ seed_dev, int R, int ld, int rows,
                                                   const double *__restrict__ g, D *__restrict__ dout) {
+    pdl_launch_dependents();
+    pdl_wait();
     if (k == 0 && seed_dev != nullptr) seed = *seed_dev;   // replayed graphs read the seed from device memory
     const int lane = threadIdx.x, ty = threadIdx.y;
     const int r = blockIdx.y * 32 + lane;
@@ -568,11 +570,11 @@ mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int 
                              const uint64_t *seed_dev) {
     dim3 block(32, 8), grid(nblk, (R + 31) / 32);
     if (dtype_bytes == 8)
-        k_prologue<double><<<grid, block, 0, st>>>(lz, k, m, seed, seed_dev, R, ld, rows, g,
-                                                   static_cast<double *>(dout));
+        launch_pdl(k_prologue<double>, grid, block, 0, st, lz, k, m, seed, seed_dev, R, ld, rows, g,
+                   static_cast<double *>(dout));
     else
-        k_prologue<float><<<grid, block, 0, st>>>(lz, k, m, seed, seed_dev, R, ld, rows, g,
-                                                  static_cast<float *>(dout));
+        launch_pdl(k_prologue<float>, grid, block, 0, st, lz, k, m, seed, seed_dev, R, ld, rows, g,
+                   static_cast<float *>(dout));
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }

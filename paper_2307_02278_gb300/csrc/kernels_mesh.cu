@@ -313,8 +313,10 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
     __shared__ double bsum[NLOC];
     __shared__ double pcarry[3 * NLOC > kWarps * 32 ? 3 * NLOC - kWarps * 32 : 1];
     __shared__ double pall[3 * NLOC];
+    pdl_launch_dependents();
     for (int k = threadIdx.x; k < (3 * NLOC > kWarps * 32 ? 3 * NLOC - kWarps * 32 : 1); k += blockDim.x)
         pcarry[k] = 0.0;
+    pdl_wait();
     double part = 0.0;                          // y.l of the (component, probe) this thread owns
     for (int ai = 0; ai < apb; ++ai) {
         const int idx = blockIdx.x * apb + ai;
@@ -704,7 +706,7 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     const int vec = field_vec(ld, (int)sizeof(T));
     const int apb = field_apb(s, ld);
     dim3 grid(field_blocks(s, ld), (ld + 32 * vec - 1) / (32 * vec));
-#define MBD_FIELD_LAUNCH(V, P) k_field<T, V, P><<<grid, kWarps * 32, 0, s->stream>>>(a, apb)
+#define MBD_FIELD_LAUNCH(V, P) launch_pdl(k_field<T, V, P>, grid, dim3(kWarps * 32), 0, s->stream, a, apb)
     if (vec == 4) {
         if constexpr (sizeof(T) == 4) {
             if (s->p == 6) MBD_FIELD_LAUNCH(4, 6);

@@ -45,6 +45,35 @@ void set_last_error(const char *where, cudaError_t e);
         }                                                                \
     } while (0)
 #define MBD_LAUNCH_CHECK() MBD_CUDA_TRY(cudaGetLastError())
+
+// Programmatic dependent launch of the kernels of a Lanczos step: each may be
+// scheduled while its predecessor in the stream runs its last blocks.  A
+// kernel lets its successor launch at once (pdl_launch_dependents, its first
+// instruction) and waits for its predecessor's completion and memory
+// (pdl_wait) before it touches global data.  The successor launches only when
+// every block of the kernel has started, so its early blocks take resources
+// only from the kernel's tail.  Both are no-ops for kernels launched without
+// the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
+}
 #define MBD_TRY(expr)                       \
     do {                                    \
         mbd_status s_ = (expr);             \
