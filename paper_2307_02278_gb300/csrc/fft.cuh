@@ -397,21 +397,25 @@ template <class T, int K, int... RS> int ct_size(const FFTArgs<T> &a, bool fused
 }
 
 // Spreading fused with the forward FFT along k3: a block owns one (k1, k2)
-// pencil of K mesh points and W complex probe-pair columns.  The block's
-// 32 / W row chains per warp spread rows k3 = chain, chain + NSG, ... (two
-// rows per iteration: two independent load chains) straight into the
-// shared-memory tile, with the records and order of k_spread_csr; then the
-// block transforms the tile along k3 and writes it once.  Probe columns >= R
-// are masked to zero.
-template <class T, int K, int W, int NT, int... RS>
+// pencil of K mesh points and W complex probe-pair columns.  A lane takes CPL
+// adjacent columns (CPL = 2: float tiles of 32 columns, one 16-byte dipole
+// load per component for four probes), so a warp holds 32 CPL / W row chains.
+// The chains spread rows k3 = chain, chain + NSG, ... (two rows per
+// iteration: two independent load chains) straight into the shared-memory
+// tile, with the records and order of k_spread_csr; then the block transforms
+// the tile along k3 and writes it once.  Probe columns >= R are masked to zero.
+template <class T, int K, int W, int NT, int CPL, int... RS>
 __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typename Cplx<T>::type *__restrict__ mesh,
                                                     int R, int ld, int K2, const int *__restrict__ row,
                                                     const SpreadRec<T> *__restrict__ rec,
                                                     const typename Cplx<T>::type *__restrict__ twg) {
     using C = typename Cplx<T>::type;
-    static_assert(32 % W == 0, "a warp holds whole row chains");
-    constexpr int G = 32 / W;                 // row chains per warp
+    constexpr int LPC = W / CPL;              // lanes per row chain
+    static_assert(W % CPL == 0 && 32 % LPC == 0, "a warp holds whole row chains");
+    static_assert(CPL == 1 || sizeof(T) == 4, "column pairs per lane are float tiles");
+    constexpr int G = 32 / LPC;               // row chains per warp
     constexpr int NSG = (NT / 32) * G;        // row chains per block
+    constexpr int NP = 2 * CPL;               // probes per lane
     extern __shared__ __align__(16) unsigned char smem_sf[];
     C *buf0 = reinterpret_cast<C *>(smem_sf);
     C *buf1 = buf0 + K * W;
@@ -424,10 +428,12 @@ __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typ
     const size_t pencil = blockIdx.x / ncb;              // k1 * K2 + k2
     const int c0 = (int)(blockIdx.x % ncb) * W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cl = lane % W, chain = warp * G + lane / W;
-    const int col = c0 + cl;                             // complex column = probes 2 col, 2 col + 1
+    const int cl = (lane % LPC) * CPL, chain = warp * G + lane / LPC;
+    const int col = c0 + cl;                             // complex columns col .. col + CPL - 1 = probes 2 col ..
     const bool on = col < V;
-    const T m0 = (2 * col < R) ? T(1) : T(0), m1 = (2 * col + 1 < R) ? T(1) : T(0);
+    T msk[NP];
+#pragma unroll
+    for (int e = 0; e < NP; ++e) msk[e] = (2 * col + e < R) ? T(1) : T(0);
     for (int k3 = chain; k3 < K; k3 += 2 * NSG) {
         const int kb = k3 + NSG;
         const size_t pa = pencil * K + k3, pb = pencil * K + kb;
@@ -438,7 +444,9 @@ __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typ
             qb = row[pb];
             qb1 = row[pb + 1];
         }
-        T ax = T(0), ay = T(0), bx = T(0), by = T(0);
+        T acc_a[NP], acc_b[NP];
+#pragma unroll
+        for (int e = 0; e < NP; ++e) acc_a[e] = acc_b[e] = T(0);
         // the next record of each row is loaded one iteration ahead, so that its
         // latency overlaps the current record's dipole loads
         SpreadRec<T> wa{}, wb{};
@@ -451,33 +459,39 @@ __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typ
             if (hb && qb + 1 < qb1) nb = rec[qb + 1];
             if (ha) {
                 if (on) {
-                    T x[2], y[2], z[2];
+                    T x[NP], y[NP], z[NP];
                     const T *dj = d + (size_t)(3 * wa.atom) * ld + 2 * col;
-                    vload<T, 2>(dj, x);
-                    vload<T, 2>(dj + ld, y);
-                    vload<T, 2>(dj + 2 * (size_t)ld, z);
-                    ax += wa.w0 * x[0] + wa.w1 * y[0] + wa.w2 * z[0];
-                    ay += wa.w0 * x[1] + wa.w1 * y[1] + wa.w2 * z[1];
+                    vload<T, NP>(dj, x);
+                    vload<T, NP>(dj + ld, y);
+                    vload<T, NP>(dj + 2 * (size_t)ld, z);
+#pragma unroll
+                    for (int e = 0; e < NP; ++e) acc_a[e] += wa.w0 * x[e] + wa.w1 * y[e] + wa.w2 * z[e];
                 }
                 ++qa;
             }
             if (hb) {
                 if (on) {
-                    T x[2], y[2], z[2];
+                    T x[NP], y[NP], z[NP];
                     const T *dj = d + (size_t)(3 * wb.atom) * ld + 2 * col;
-                    vload<T, 2>(dj, x);
-                    vload<T, 2>(dj + ld, y);
-                    vload<T, 2>(dj + 2 * (size_t)ld, z);
-                    bx += wb.w0 * x[0] + wb.w1 * y[0] + wb.w2 * z[0];
-                    by += wb.w0 * x[1] + wb.w1 * y[1] + wb.w2 * z[1];
+                    vload<T, NP>(dj, x);
+                    vload<T, NP>(dj + ld, y);
+                    vload<T, NP>(dj + 2 * (size_t)ld, z);
+#pragma unroll
+                    for (int e = 0; e < NP; ++e) acc_b[e] += wb.w0 * x[e] + wb.w1 * y[e] + wb.w2 * z[e];
                 }
                 ++qb;
             }
             wa = na;
             wb = nb;
         }
-        buf0[k3 * W + cl] = on ? C{ax * m0, ay * m1} : C{T(0), T(0)};
-        if (kb < K) buf0[kb * W + cl] = on ? C{bx * m0, by * m1} : C{T(0), T(0)};
+#pragma unroll
+        for (int u = 0; u < CPL; ++u) {
+            buf0[k3 * W + cl + u] = on ? C{acc_a[2 * u] * msk[2 * u], acc_a[2 * u + 1] * msk[2 * u + 1]}
+                                       : C{T(0), T(0)};
+            if (kb < K)
+                buf0[kb * W + cl + u] = on ? C{acc_b[2 * u] * msk[2 * u], acc_b[2 * u + 1] * msk[2 * u + 1]}
+                                           : C{T(0), T(0)};
+        }
     }
     __syncthreads();
     const int wc = min(W, V - c0);
@@ -486,21 +500,32 @@ __global__ void __launch_bounds__(NT) k_spread_fft3(const T *__restrict__ d, typ
                                                               (const T *)nullptr, 0, c0, V);
 }
 
-template <class T, int K, int W, int... RS>
-int launch_sf3(const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row, const SpreadRec<T> *rec,
-               const typename Cplx<T>::type *tw, cudaStream_t st) {
+template <class T, int K, int W, int CPL, int... RS>
+int launch_sf3_cpl(const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row, const SpreadRec<T> *rec,
+                   const typename Cplx<T>::type *tw, cudaStream_t st) {
     using C = typename Cplx<T>::type;
     constexpr int NT = ct_threads<K, W, RS...>();
     const size_t smem = sizeof(C) * (2 * (size_t)K * W + K);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_spread_fft3<T, K, W, NT, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_spread_fft3<T, K, W, NT, CPL, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
     const int V = ld / 2;
     const unsigned grid = (unsigned)((size_t)K1 * K2 * ((V + W - 1) / W));
-    launch_pdl(k_spread_fft3<T, K, W, NT, RS...>, dim3(grid), dim3(NT), smem, st, d, reinterpret_cast<C *>(mesh), R,
-               ld, K2, row, rec, tw);
+    launch_pdl(k_spread_fft3<T, K, W, NT, CPL, RS...>, dim3(grid), dim3(NT), smem, st, d,
+               reinterpret_cast<C *>(mesh), R, ld, K2, row, rec, tw);
     return 1;
+}
+
+// Float tiles of 32 columns take two columns per lane when the dipole rows
+// allow 16-byte loads (ld a multiple of 4).
+template <class T, int K, int W, int... RS>
+int launch_sf3(const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row, const SpreadRec<T> *rec,
+               const typename Cplx<T>::type *tw, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4 && W == 32) {
+        if (ld % 4 == 0) return launch_sf3_cpl<T, K, W, 2, RS...>(d, mesh, R, ld, K1, K2, row, rec, tw, st);
+    }
+    return launch_sf3_cpl<T, K, W, 1, RS...>(d, mesh, R, ld, K1, K2, row, rec, tw, st);
 }
 
 template <class T, int K, int... RS>
