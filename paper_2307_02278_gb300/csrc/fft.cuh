@@ -19,6 +19,7 @@ template <class T> struct FFTArgs {
     unsigned long long radices;   // stage s radix = (radices >> 4 s) & 15
     int V;               // complex probe pairs per mesh point (fused pass: G index = e / V)
     int sign;            // -1 forward, +1 inverse (unfused passes)
+    int early;           // compile-time passes: programmatic dependent launch (1) or plain (0)
 };
 
 // Compile-time passes for the smooth sizes listed below (fft_sizes_*.cu).
@@ -366,7 +367,7 @@ template <class T, bool FUSED, int K, int W, int CV, int... RS> int launch_ct_cv
         cudaFuncSetAttribute(k_fft_ct<T, FUSED, K, W, NT, CV, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
-    launch_pdl(k_fft_ct<T, FUSED, K, W, NT, CV, RS...>, dim3(grid), dim3(NT), smem, st, a);
+    launch_pdl(a.early != 0, k_fft_ct<T, FUSED, K, W, NT, CV, RS...>, dim3(grid), dim3(NT), smem, st, a);
     return 1;
 }
 
@@ -512,7 +513,7 @@ int launch_sf3_cpl(const T *d, T *mesh, int R, int ld, int K1, int K2, const int
         return 0;
     const int V = ld / 2;
     const unsigned grid = (unsigned)((size_t)K1 * K2 * ((V + W - 1) / W));
-    launch_pdl(k_spread_fft3<T, K, W, NT, CPL, RS...>, dim3(grid), dim3(NT), smem, st, d,
+    launch_pdl(true, k_spread_fft3<T, K, W, NT, CPL, RS...>, dim3(grid), dim3(NT), smem, st, d,
                reinterpret_cast<C *>(mesh), R, ld, K2, row, rec, tw);
     return 1;
 }

@@ -570,11 +570,11 @@ mbd_status launch_prologue_t(cudaStream_t st, const LanczosView &lz, int k, int 
                              const uint64_t *seed_dev) {
     dim3 block(32, 8), grid(nblk, (R + 31) / 32);
     if (dtype_bytes == 8)
-        launch_pdl(k_prologue<double>, grid, block, 0, st, lz, k, m, seed, seed_dev, R, ld, rows, g,
-                   static_cast<double *>(dout));
+        k_prologue<double><<<grid, block, 0, st>>>(lz, k, m, seed, seed_dev, R, ld, rows, g,
+                                                   static_cast<double *>(dout));
     else
-        launch_pdl(k_prologue<float>, grid, block, 0, st, lz, k, m, seed, seed_dev, R, ld, rows, g,
-                   static_cast<float *>(dout));
+        k_prologue<float><<<grid, block, 0, st>>>(lz, k, m, seed, seed_dev, R, ld, rows, g,
+                                                  static_cast<float *>(dout));
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }

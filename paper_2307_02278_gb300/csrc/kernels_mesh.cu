@@ -554,6 +554,10 @@ template <class T> mbd_status launch_spread(mbd_system *s, const T *d, T *mesh, 
     return MBD_OK;
 }
 
+// Meshes of at most this many bytes (three quarters of the 129 MB L2) launch
+// their FFT passes with programmatic dependence; larger ones plainly.
+constexpr size_t kEarlyFFTMaxBytes = 96u << 20;
+
 // FP32 passes and fused spreading over meshes longer than this use tiles of
 // 16 complex columns instead of 32: half the shared memory per block, twice
 // the resident blocks, which the long (latency-bound) spreading phase needs.
@@ -635,6 +639,7 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bo
     const int V = ld / 2;
     const int K1 = s->K[0], K2 = s->K[1], K3 = s->K[2];
     const int Wmax = sizeof(T) == 4 ? 32 : 16;
+    const size_t npts_bytes = sizeof(T) * (size_t)K1 * K2 * K3 * ld;
     auto run = [&](int dim, int outer, int inner, int sign, bool fused) -> mbd_status {
         FFTArgs<T> a;
         a.data = reinterpret_cast<C *>(mesh);
@@ -648,6 +653,8 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bo
         a.W = inner < Wmax ? inner : Wmax;
         a.V = V;
         a.sign = sign;
+        // early launch of the passes while the mesh fits in three quarters of L2
+        a.early = npts_bytes <= kEarlyFFTMaxBytes ? 1 : 0;
         // compile-time pass: float tiles of 32 complex columns (16 for narrow
         // rows and for long meshes), double tiles of 16; narrower rows are masked
         FFTArgs<T> c = a;
@@ -706,7 +713,7 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     const int vec = field_vec(ld, (int)sizeof(T));
     const int apb = field_apb(s, ld);
     dim3 grid(field_blocks(s, ld), (ld + 32 * vec - 1) / (32 * vec));
-#define MBD_FIELD_LAUNCH(V, P) launch_pdl(k_field<T, V, P>, grid, dim3(kWarps * 32), 0, s->stream, a, apb)
+#define MBD_FIELD_LAUNCH(V, P) k_field<T, V, P><<<grid, kWarps * 32, 0, s->stream>>>(a, apb)
     if (vec == 4) {
         if constexpr (sizeof(T) == 4) {
             if (s->p == 6) MBD_FIELD_LAUNCH(4, 6);

@@ -46,22 +46,26 @@ void set_last_error(const char *where, cudaError_t e);
     } while (0)
 #define MBD_LAUNCH_CHECK() MBD_CUDA_TRY(cudaGetLastError())
 
-// Programmatic dependent launch of the kernels of a Lanczos step: each may be
-// scheduled while its predecessor in the stream runs its last blocks.  A
-// kernel lets its successor launch at once (pdl_launch_dependents, its first
-// instruction) and waits for its predecessor's completion and memory
-// (pdl_wait) before it touches global data.  The successor launches only when
-// every block of the kernel has started, so its early blocks take resources
-// only from the kernel's tail.  Both are no-ops for kernels launched without
-// the attribute.
+// Programmatic dependent launch in a Lanczos step: a kernel launched with it
+// may be scheduled while its predecessor in the stream runs its last blocks.
+// The kernels of the step let their successor launch at once
+// (pdl_launch_dependents, their first instruction) and wait for their
+// predecessor's completion and memory (pdl_wait) before they touch global
+// data.  The successor launches only when every block of the predecessor has
+// started, so its early blocks take resources only from the predecessor's
+// tail.  Both instructions are no-ops in a kernel launched without the
+// attribute.  Measured per kernel: early launch helps the fused spreading
+// (after the prologue) and the FFT passes while the mesh fits in L2; it slows
+// the FFT passes on meshes beyond L2, and the prologue and field kernels at
+// every size, which are therefore launched plainly.
 __device__ __forceinline__ void pdl_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <class... KArgs, class... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                              Args &&...args) {
+inline cudaError_t launch_pdl(bool early, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -71,7 +75,7 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = early ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<Args &&>(args)...);
 }
 #define MBD_TRY(expr)                       \
