@@ -186,6 +186,16 @@ void wrap_positions(mbd_system *s, const double *pos) {
 // Full neighbour list over image pairs (i, j, n) with 0 < |R_i - R_j - n| < rmax
 // from a cell list: bins of perpendicular width >= rmax; bin offsets o map to
 // (o mod nbins, floor(o / nbins)) = (bin, image), so each (j, n) is visited once.
+// Neighbour-list and pair-tensor capacity for nnz pairs, with a quarter more
+// room so that small changes of the list between steps need no reallocation.
+mbd_status size_pair_buffers(mbd_system *s, long long nnz) {
+    const long long cap = std::max<long long>(1, nnz + nnz / 4 + 32);
+    MBD_TRY(s->col_d.ensure(sizeof(int) * (size_t)cap));
+    MBD_TRY(s->shift_d.ensure(sizeof(int) * (size_t)cap));
+    s->nb_cap = cap;
+    return MBD_OK;
+}
+
 mbd_status build_neighbors(mbd_system *s) {
     const double rmax = std::max(s->r_cut, s->damp_cut);
     const int N = s->N;
@@ -236,23 +246,25 @@ mbd_status build_neighbors(mbd_system *s) {
     ng.cidx = s->cell_idx_d.as<int>();
     for (int k = 0; k < 9; ++k) ng.cell[k] = s->cell[k];
     ng.r2max = rmax * rmax;
-    DevBuf cnt, bsum;
-    MBD_TRY(cnt.ensure(sizeof(int) * std::max(1, N)));
-    MBD_TRY(launch_neighbors(ng, s->pos_d.as<double>(), cnt.as<int>(), nullptr, nullptr, s->nb_err_d.as<int>(),
-                             false, s->stream));
-    MBD_TRY(launch_exclusive_scan(cnt.as<int>(), s->row_d.as<int>(), N, bsum, s->stream));
-    int head[2] = {0, 0};
-    MBD_CUDA_TRY(cudaMemcpyAsync(&head[0], s->row_d.as<int>() + N, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    MBD_CUDA_TRY(cudaMemcpyAsync(&head[1], s->nb_err_d.ptr, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
-    if (head[0] < 0 || head[1] != 0) return MBD_ERR_INVALID_ARG;
-    s->nnz = head[0];
-    MBD_TRY(s->col_d.ensure(sizeof(int) * std::max<size_t>(1, (size_t)s->nnz)));
-    MBD_TRY(s->shift_d.ensure(sizeof(int) * std::max<size_t>(1, (size_t)s->nnz)));
-    MBD_TRY(launch_neighbors(ng, s->pos_d.as<double>(), s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(),
-                             s->nb_err_d.as<int>(), true, s->stream));
-    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));   // cnt and bsum are freed on return
-    return MBD_OK;
+    s->ngrid = ng;
+    MBD_TRY(s->scan_cnt.ensure(sizeof(int) * std::max(1, N)));
+    MBD_TRY(launch_neighbors(ng, s->pos_d.as<double>(), s->scan_cnt.as<int>(), nullptr, nullptr,
+                             s->nb_err_d.as<int>(), false, 0, s->stream));
+    MBD_TRY(launch_exclusive_scan(s->scan_cnt.as<int>(), s->row_d.as<int>(), N, s->scan_bsum, s->stream));
+    if (s->nb_cap == 0) {
+        // first build: the list is sized from its count (with room to grow)
+        int head[2] = {0, 0};
+        MBD_CUDA_TRY(cudaMemcpyAsync(&head[0], s->row_d.as<int>() + N, sizeof(int), cudaMemcpyDeviceToHost,
+                                     s->stream));
+        MBD_CUDA_TRY(cudaMemcpyAsync(&head[1], s->nb_err_d.ptr, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (head[0] < 0 || head[1] != 0) return MBD_ERR_INVALID_ARG;
+        MBD_TRY(size_pair_buffers(s, head[0]));
+    }
+    // later builds keep the buffers and find out at the end whether the list
+    // still fits them (setup_geometry)
+    return launch_neighbors(ng, s->pos_d.as<double>(), s->row_d.as<int>(), s->col_d.as<int>(),
+                            s->shift_d.as<int>(), s->nb_err_d.as<int>(), true, s->nb_cap, s->stream);
 }
 
 // Bricks of the mesh for deterministic spreading; atoms are binned by the
@@ -260,9 +272,6 @@ mbd_status build_neighbors(mbd_system *s) {
 // the host and the kernels agree exactly.
 mbd_status build_bins(mbd_system *s) {
     const int N = s->N;
-    std::vector<int> top(3 * (size_t)N);
-    MBD_CUDA_TRY(cudaMemcpyAsync(top.data(), s->top_d.ptr, sizeof(int) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
-    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
     int bs[3], nb[3], ncand[3];
     for (int a = 0; a < 3; ++a) {
         const int K = s->K[a];
@@ -277,25 +286,12 @@ mbd_status build_bins(mbd_system *s) {
         ncand[a] = std::min(nb[a], 1 + (bs[a] + s->p - 2) / bs[a]);
     }
     const int nbins = nb[0] * nb[1] * nb[2];
-    std::vector<int> start(nbins + 1, 0), atoms(N), bin(N);
-    for (int i = 0; i < N; ++i) {
-        const int t0 = top[3 * i] / bs[0], t1 = top[3 * i + 1] / bs[1], t2 = top[3 * i + 2] / bs[2];
-        bin[i] = (t0 * nb[1] + t1) * nb[2] + t2;
-        start[bin[i] + 1]++;
-    }
-    for (int b = 0; b < nbins; ++b) start[b + 1] += start[b];
-    {
-        std::vector<int> fill(start.begin(), start.end() - 1);
-        for (int i = 0; i < N; ++i) atoms[fill[bin[i]]++] = i;
-    }
     MBD_TRY(s->bin_start_d.ensure(sizeof(int) * (nbins + 1)));
-    MBD_TRY(s->bin_atoms_d.ensure(sizeof(int) * N));
-    MBD_TRY(s->order_d.ensure(sizeof(int) * N));
-    MBD_CUDA_TRY(cudaMemcpyAsync(s->bin_start_d.ptr, start.data(), sizeof(int) * (nbins + 1), cudaMemcpyHostToDevice,
-                                 s->stream));
-    MBD_CUDA_TRY(cudaMemcpyAsync(s->bin_atoms_d.ptr, atoms.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s->stream));
-    MBD_CUDA_TRY(cudaMemcpyAsync(s->order_d.ptr, atoms.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s->stream));
-    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    MBD_TRY(s->bin_atoms_d.ensure(sizeof(int) * std::max(1, N)));
+    MBD_TRY(s->order_d.ensure(sizeof(int) * std::max(1, N)));
+    MBD_TRY(s->bin_of_d.ensure(sizeof(int) * std::max(1, N)));
+    MBD_TRY(s->bin_cursor_d.ensure(sizeof(int) * nbins));
+    MBD_TRY(s->scan_cnt.ensure(sizeof(int) * std::max(nbins, N)));
     BinView &B = s->bins;
     B.nb1 = nb[0];
     B.nb2 = nb[1];
@@ -308,6 +304,13 @@ mbd_status build_bins(mbd_system *s) {
     B.nc3 = ncand[2];
     B.start = s->bin_start_d.as<int>();
     B.atoms = s->bin_atoms_d.as<int>();
+    MBD_TRY(launch_bin_atoms(N, s->top_d.as<int>(), B, s->bin_of_d.as<int>(), s->scan_cnt.as<int>(),
+                             s->bin_start_d.as<int>(), s->bin_cursor_d.as<int>(), s->bin_atoms_d.as<int>(),
+                             s->scan_bsum, s->stream));
+    // the field kernel takes the atoms in the same (spatially sorted) order
+    if (N > 0)
+        MBD_CUDA_TRY(cudaMemcpyAsync(s->order_d.ptr, s->bin_atoms_d.ptr, sizeof(int) * N, cudaMemcpyDeviceToDevice,
+                                     s->stream));
     return MBD_OK;
 }
 
@@ -360,6 +363,10 @@ template <class T> mbd_status upload_twiddles(mbd_system *s) {
     return MBD_OK;
 }
 
+// Positions to neighbour list, pair tensors, splines, bricks and spreading
+// matrix, all queued on the stream; one readback at the end gives the pair
+// count and the error flags.  A list that outgrew its buffers is filled again
+// into larger ones, with its pair tensors.
 template <class T> mbd_status setup_geometry(mbd_system *s) {
     MBD_CUDA_TRY(cudaMemcpyAsync(s->pos_d.ptr, s->pos.data(), sizeof(double) * 3 * s->N, cudaMemcpyHostToDevice,
                                  s->stream));
@@ -368,7 +375,20 @@ template <class T> mbd_status setup_geometry(mbd_system *s) {
     MBD_TRY(launch_splines<T>(s, s->stream));
     MBD_TRY(build_bins(s));
     MBD_TRY(build_spread_matrix<T>(s));
+    int head[2] = {0, 0};
+    MBD_CUDA_TRY(cudaMemcpyAsync(&head[0], s->row_d.as<int>() + s->N, sizeof(int), cudaMemcpyDeviceToHost,
+                                 s->stream));
+    MBD_CUDA_TRY(cudaMemcpyAsync(&head[1], s->nb_err_d.ptr, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (head[0] < 0 || head[1] != 0) return MBD_ERR_INVALID_ARG;
+    s->nnz = head[0];
+    if (s->nnz > s->nb_cap) {
+        MBD_TRY(size_pair_buffers(s, s->nnz));
+        MBD_TRY(launch_neighbors(s->ngrid, s->pos_d.as<double>(), s->row_d.as<int>(), s->col_d.as<int>(),
+                                 s->shift_d.as<int>(), s->nb_err_d.as<int>(), true, s->nb_cap, s->stream));
+        MBD_TRY(launch_pair_tensors<T>(s, s->stream));
+        MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    }
     return MBD_OK;
 }
 

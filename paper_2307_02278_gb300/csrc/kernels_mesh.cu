@@ -519,7 +519,7 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s) {
     if (nnz >= 0x7fffffffULL) return MBD_ERR_UNSUPPORTED;
     MBD_TRY(P.srow.ensure(sizeof(int) * (npts + 1)));
     MBD_TRY(P.srec.ensure(sizeof(SpreadRec<T>) * std::max<size_t>(1, nnz)));
-    DevBuf cnt, bsum;
+    DevBuf &cnt = s->scan_cnt, &bsum = s->scan_bsum;
     MBD_TRY(cnt.ensure(sizeof(int) * npts));
     const int threads = 256;
     const unsigned blocks = (unsigned)((npts + threads - 1) / threads);
@@ -531,7 +531,6 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s) {
                                                              s->dw64_d.as<double>(), P.srow.template as<int>(),
                                                              P.srec.template as<SpreadRec<T>>());
     MBD_LAUNCH_CHECK();
-    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));   // cnt and bsum are freed on return
     return MBD_OK;
 }
 

@@ -3,6 +3,7 @@
 // mbd_update_positions), not per Lanczos step.
 #include "mbd_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace mbd {
@@ -82,12 +83,13 @@ __global__ void k_pair_tensors(int N, const double *__restrict__ pos, const doub
                                const int *__restrict__ row, const int *__restrict__ col,
                                const int *__restrict__ shift, Geom g, double beta, double r_cut,
                                double damp_cut, double damp_beta, double damp_d, T *__restrict__ A,
-                               T *__restrict__ dA) {
+                               T *__restrict__ dA, long long cap) {
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= N) return;
     const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
-    for (int nb = row[i] + lane; nb < row[i + 1]; nb += 32) {
+    const int nb1 = (int)min((long long)row[i + 1], cap);   // pairs beyond the buffers: rebuilt by the caller
+    for (int nb = row[i] + lane; nb < nb1; nb += 32) {
         const int j = col[nb];
         const int sh = shift[nb];
         const double n1 = double((sh & 255) - 128), n2 = double(((sh >> 8) & 255) - 128),
@@ -223,12 +225,12 @@ Geom make_geom(const mbd_system *s) {
 // visits the cells c = cidx(i) + o, o in [-kk, kk]^3, with their lattice
 // image n; the lanes take the atoms of each cell 32 at a time, and a ballot
 // keeps the hits in cell order, then atom order.  FILL = false counts, FILL =
-// true writes (j, packed n).  The order is fixed, so the list is the same on
-// every run.  err bit 1: an image index beyond +-127.
+// true writes (j, packed n) for the pairs below cap.  The order is fixed, so
+// the list is the same on every run.  err bit 1: an image index beyond +-127.
 template <bool FILL>
 __global__ void __launch_bounds__(128) k_neighbors(NeighborGrid ng, const double *__restrict__ pos,
                                                    int *__restrict__ cnt_or_row, int *__restrict__ col,
-                                                   int *__restrict__ shift, int *__restrict__ err) {
+                                                   int *__restrict__ shift, int *__restrict__ err, long long cap) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (i >= ng.N) return;
@@ -268,8 +270,10 @@ __global__ void __launch_bounds__(128) k_neighbors(NeighborGrid ng, const double
                     if (hit && far && !FILL) atomicOr(err, 1);
                     if (FILL && hit && !far) {
                         const int at = base + c + __popc(bal & ((1u << lane) - 1u));
-                        col[at] = j;
-                        shift[at] = (n0 + 128) | ((n1 + 128) << 8) | ((n2 + 128) << 16);
+                        if (at < cap) {
+                            col[at] = j;
+                            shift[at] = (n0 + 128) | ((n1 + 128) << 8) | ((n2 + 128) << 16);
+                        }
                     }
                     c += __popc(bal);
                 }
@@ -287,16 +291,17 @@ template <> PrecData<float> &prec<float>(mbd_system *s) { return s->f32; }
 
 template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st) {
     PrecData<T> &P = prec<T>(s);
-    MBD_TRY(P.pairA.ensure(sizeof(T) * 6 * (size_t)(s->nnz > 0 ? s->nnz : 1)));
-    MBD_TRY(P.pairdA.ensure(sizeof(T) * 18 * (size_t)(s->nnz > 0 ? s->nnz : 1)));
-    if (s->nnz == 0) return MBD_OK;
+    const size_t cap = (size_t)std::max<long long>(1, s->nb_cap);
+    MBD_TRY(P.pairA.ensure(sizeof(T) * 6 * cap));
+    MBD_TRY(P.pairdA.ensure(sizeof(T) * 18 * cap));
     const Geom g = make_geom(s);
     const int threads = 256;
     const int blocks = (int)(((long long)s->N * 32 + threads - 1) / threads);
     k_pair_tensors<T><<<blocks, threads, 0, st>>>(s->N, s->pos_d.as<double>(), s->rvdw_d.as<double>(),
                                                   s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(), g,
                                                   s->ewald_beta, s->r_cut, s->damp_cut, s->damp_beta, s->damp_d,
-                                                  P.pairA.template as<T>(), P.pairdA.template as<T>());
+                                                  P.pairA.template as<T>(), P.pairdA.template as<T>(),
+                                                  (long long)cap);
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }
@@ -336,14 +341,67 @@ template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod
 }
 
 mbd_status launch_neighbors(const NeighborGrid &ng, const double *pos, int *cnt_or_row, int *col, int *shift,
-                            int *err, bool fill, cudaStream_t st) {
+                            int *err, bool fill, long long cap, cudaStream_t st) {
     const unsigned blocks = (unsigned)((ng.N + 3) / 4);   // a warp per atom
     if (ng.N == 0) return MBD_OK;
     if (fill)
-        k_neighbors<true><<<blocks, 128, 0, st>>>(ng, pos, cnt_or_row, col, shift, err);
+        k_neighbors<true><<<blocks, 128, 0, st>>>(ng, pos, cnt_or_row, col, shift, err, cap);
     else
-        k_neighbors<false><<<blocks, 128, 0, st>>>(ng, pos, cnt_or_row, col, shift, err);
+        k_neighbors<false><<<blocks, 128, 0, st>>>(ng, pos, cnt_or_row, col, shift, err, cap);
     MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+namespace {
+// Brick of each atom (of its top stencil point) and the atoms per brick.
+__global__ void k_bin_count(int N, const int *__restrict__ top, BinView B, int *__restrict__ bin_of,
+                            int *__restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = (top[3 * i] / B.bs1 * B.nb2 + top[3 * i + 1] / B.bs2) * B.nb3 + top[3 * i + 2] / B.bs3;
+    bin_of[i] = b;
+    atomicAdd(&cnt[b], 1);
+}
+// Each atom takes a slot of its brick (in arrival order) ...
+__global__ void k_bin_fill(int N, const int *__restrict__ bin_of, int *__restrict__ cursor, int *__restrict__ atoms) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    atoms[atomicAdd(&cursor[bin_of[i]], 1)] = i;
+}
+// ... and each brick's atoms are then put in increasing index order, so the
+// lists do not depend on the arrival order.
+__global__ void k_bin_sort(int nbins, const int *__restrict__ start, int *__restrict__ atoms) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int q0 = start[b], q1 = start[b + 1];
+    for (int q = q0 + 1; q < q1; ++q) {
+        const int v = atoms[q];
+        int r = q - 1;
+        while (r >= q0 && atoms[r] > v) {
+            atoms[r + 1] = atoms[r];
+            --r;
+        }
+        atoms[r + 1] = v;
+    }
+}
+}  // namespace
+
+mbd_status launch_bin_atoms(int N, const int *top, const BinView &B, int *bin_of, int *cnt, int *start,
+                            int *cursor, int *atoms, DevBuf &bsum, cudaStream_t st) {
+    const int nbins = B.nb1 * B.nb2 * B.nb3;
+    MBD_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * nbins, st));
+    if (N > 0) {
+        k_bin_count<<<(N + 255) / 256, 256, 0, st>>>(N, top, B, bin_of, cnt);
+        MBD_LAUNCH_CHECK();
+    }
+    MBD_TRY(launch_exclusive_scan(cnt, start, nbins, bsum, st));
+    MBD_CUDA_TRY(cudaMemcpyAsync(cursor, start, sizeof(int) * nbins, cudaMemcpyDeviceToDevice, st));
+    if (N > 0) {
+        k_bin_fill<<<(N + 255) / 256, 256, 0, st>>>(N, bin_of, cursor, atoms);
+        MBD_LAUNCH_CHECK();
+        k_bin_sort<<<(nbins + 255) / 256, 256, 0, st>>>(nbins, start, atoms);
+        MBD_LAUNCH_CHECK();
+    }
     return MBD_OK;
 }
 

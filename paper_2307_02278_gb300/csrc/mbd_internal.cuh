@@ -113,6 +113,17 @@ template <class T> struct SplineView {
     const T *d2w;       // [N][3][p] (forces only)
 };
 
+// Cell grid of the neighbour search (built on the host, searched on the device).
+struct NeighborGrid {
+    int N;
+    int nc[3], kk[3];       // cells per direction; cells searched each way
+    const int *start;       // [ncell + 1]
+    const int *atoms;       // [N] atoms by cell
+    const int *cidx;        // [N][3] cell coordinates of each atom
+    double cell[9];
+    double r2max;
+};
+
 struct BinView {
     int nb1, nb2, nb3;      // bricks (= bins) per dimension
     int bs1, bs2, bs3;      // brick edge (mesh points)
@@ -268,6 +279,10 @@ struct mbd_system {
     mbd::DevBuf top_d;                              // [N][3]
     mbd::DevBuf w64_d, dw64_d;                      // [N][3][p] FP64 stencil weights (setup)
     mbd::DevBuf bin_start_d, bin_atoms_d, order_d;  // spread bins; field atom order
+    mbd::DevBuf bin_of_d, bin_cursor_d;             // [N] brick of each atom, [nbins] fill cursors
+    mbd::DevBuf scan_cnt, scan_bsum;                // count / scan scratch of the geometry setup
+    long long nb_cap = 0;   // pairs col_d, shift_d and the pair tensors hold (0: not sized yet)
+    mbd::NeighborGrid ngrid{};   // the last neighbour search's grid
     mbd::BinView bins;
     long long nnz;
     // precision-specific
@@ -289,17 +304,13 @@ namespace mbd {
 
 // ---------------------------------------------------------------- launchers (kernels_*.cu)
 // setup
-struct NeighborGrid {
-    int N;
-    int nc[3], kk[3];       // cells per direction; cells searched each way
-    const int *start;       // [ncell + 1]
-    const int *atoms;       // [N] atoms by cell
-    const int *cidx;        // [N][3] cell coordinates of each atom
-    double cell[9];
-    double r2max;
-};
+// Atoms binned by the brick of their top stencil point (B's geometry), in
+// increasing atom index within a brick: counts, starts [nbins + 1], atoms [N].
+mbd_status launch_bin_atoms(int N, const int *top, const BinView &B, int *bin_of, int *cnt, int *start,
+                            int *cursor, int *atoms, DevBuf &bsum, cudaStream_t st);
+// fill: writes the pairs below cap only (the caller compares row[N] with cap)
 mbd_status launch_neighbors(const NeighborGrid &ng, const double *pos, int *cnt_or_row, int *col, int *shift,
-                            int *err, bool fill, cudaStream_t st);
+                            int *err, bool fill, long long cap, cudaStream_t st);
 mbd_status launch_exclusive_scan(const int *in, int *out, int n, DevBuf &bsum, cudaStream_t st);
 template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st);
 template <class T> mbd_status launch_splines(mbd_system *s, cudaStream_t st);
