@@ -74,6 +74,101 @@ __global__ void k_spread_rows(Geom g, BinView B, const int *__restrict__ top, co
     if (!FILL) cnt_or_row[pt] = c;
 }
 
+// The same rows with a block per brick: the candidate atoms of the brick's
+// points (the atoms of its nc1 x nc2 x nc3 candidate bricks, in the order the
+// per-point kernel visits them) are staged once in shared memory, with their
+// top stencil points, and a thread per point of the brick tests them there.
+// The rows are identical to k_spread_rows'.  A brick with more than
+// kRowsCap candidates reads them from global memory instead.
+constexpr int kRowsCap = 512;
+constexpr int kRowsMaxBins = 512;
+template <class T, bool FILL>
+__global__ void k_spread_rows_brick(Geom g, BinView B, const int *__restrict__ top, const double *__restrict__ w64,
+                                    const double *__restrict__ dw64, int *__restrict__ cnt_or_row,
+                                    SpreadRec<T> *__restrict__ rec) {
+    __shared__ int cj[kRowsCap], ct[kRowsCap][3];
+    __shared__ int boff[kRowsMaxBins + 1], bfirst[kRowsMaxBins];
+    const int tid = threadIdx.x;
+    const int brick = blockIdx.x;
+    const int bb1 = brick / (B.nb2 * B.nb3), bb2 = (brick / B.nb3) % B.nb2, bb3 = brick % B.nb3;
+    const int nbc = B.nc1 * B.nc2 * B.nc3;
+    for (int t = tid; t < nbc; t += blockDim.x) {
+        const int c1 = t / (B.nc2 * B.nc3), c2 = (t / B.nc3) % B.nc2, c3 = t % B.nc3;
+        const int bin = (((bb1 + c1) % B.nb1) * B.nb2 + (bb2 + c2) % B.nb2) * B.nb3 + (bb3 + c3) % B.nb3;
+        bfirst[t] = B.start[bin];
+        boff[t + 1] = B.start[bin + 1] - B.start[bin];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        boff[0] = 0;
+        for (int t = 0; t < nbc; ++t) boff[t + 1] += boff[t];
+    }
+    __syncthreads();
+    const int total = boff[nbc];
+    const bool staged = total <= kRowsCap;
+    if (staged) {
+        for (int k = tid; k < total; k += blockDim.x) {
+            int lo = 0, hi = nbc - 1;   // the candidate brick holding entry k
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (boff[mid] <= k) lo = mid;
+                else hi = mid - 1;
+            }
+            const int j = B.atoms[bfirst[lo] + (k - boff[lo])];
+            cj[k] = j;
+            ct[k][0] = top[3 * j];
+            ct[k][1] = top[3 * j + 1];
+            ct[k][2] = top[3 * j + 2];
+        }
+    }
+    __syncthreads();
+    const int npb = B.bs1 * B.bs2 * B.bs3;
+    if (tid >= npb) return;
+    const int g1 = bb1 * B.bs1 + tid / (B.bs2 * B.bs3), g2 = bb2 * B.bs2 + (tid / B.bs3) % B.bs2,
+              g3 = bb3 * B.bs3 + tid % B.bs3;
+    const size_t pt = ((size_t)g1 * g.K2 + g2) * g.K3 + g3;
+    const int p = g.p;
+    int c = 0;
+    const int base = FILL ? cnt_or_row[pt] : 0;
+    for (int k = 0; k < total; ++k) {
+        int j, tj1, tj2, tj3;
+        if (staged) {
+            j = cj[k];
+            tj1 = ct[k][0];
+            tj2 = ct[k][1];
+            tj3 = ct[k][2];
+        } else {
+            int t = 0;
+            while (boff[t + 1] <= k) ++t;
+            j = B.atoms[bfirst[t] + (k - boff[t])];
+            tj1 = top[3 * j];
+            tj2 = top[3 * j + 1];
+            tj3 = top[3 * j + 2];
+        }
+        int u1 = tj1 - g1;
+        if (u1 < 0) u1 += g.K1;
+        int u2 = tj2 - g2;
+        if (u2 < 0) u2 += g.K2;
+        int u3 = tj3 - g3;
+        if (u3 < 0) u3 += g.K3;
+        if (u1 >= p || u2 >= p || u3 >= p) continue;
+        if (FILL) {
+            const double *w = w64 + (size_t)3 * p * j, *dw = dw64 + (size_t)3 * p * j;
+            const double m1 = w[u1], m2 = w[p + u2], m3 = w[2 * p + u3];
+            const double n1 = dw[u1], n2 = dw[p + u2], n3 = dw[2 * p + u3];
+            const double gu0 = n1 * m2 * m3, gu1 = m1 * n2 * m3, gu2 = m1 * m2 * n3;
+            SpreadRec<T> r;
+            r.w0 = T(g.cmat[0] * gu0 + g.cmat[3] * gu1 + g.cmat[6] * gu2);
+            r.w1 = T(g.cmat[1] * gu0 + g.cmat[4] * gu1 + g.cmat[7] * gu2);
+            r.w2 = T(g.cmat[2] * gu0 + g.cmat[5] * gu1 + g.cmat[8] * gu2);
+            r.atom = j;
+            rec[base + c] = r;
+        }
+        ++c;
+    }
+    if (!FILL) cnt_or_row[pt] = c;
+}
+
 // Exclusive scan of n counts (blocks of 4096), the block sums, and the fix-up.
 __global__ void __launch_bounds__(1024) k_scan_block(const int *__restrict__ in, int *__restrict__ out,
                                                      int *__restrict__ bsum, int n) {
@@ -522,6 +617,22 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s) {
     DevBuf &cnt = s->scan_cnt, &bsum = s->scan_bsum;
     MBD_TRY(cnt.ensure(sizeof(int) * npts));
     const int threads = 256;
+    const BinView &B = s->bins;
+    const int npb = B.bs1 * B.bs2 * B.bs3;
+    if (B.nc1 * B.nc2 * B.nc3 <= kRowsMaxBins && npb <= 1024) {
+        // a block per brick
+        const unsigned nbricks = (unsigned)(B.nb1 * B.nb2 * B.nb3);
+        const unsigned bt = (unsigned)((npb + 31) / 32 * 32);
+        k_spread_rows_brick<T, false><<<nbricks, bt, 0, s->stream>>>(g, B, s->top_d.as<int>(), s->w64_d.as<double>(),
+                                                                    s->dw64_d.as<double>(), cnt.as<int>(), nullptr);
+        MBD_LAUNCH_CHECK();
+        MBD_TRY(launch_exclusive_scan(cnt.as<int>(), P.srow.template as<int>(), (int)npts, bsum, s->stream));
+        k_spread_rows_brick<T, true><<<nbricks, bt, 0, s->stream>>>(g, B, s->top_d.as<int>(), s->w64_d.as<double>(),
+                                                                   s->dw64_d.as<double>(), P.srow.template as<int>(),
+                                                                   P.srec.template as<SpreadRec<T>>());
+        MBD_LAUNCH_CHECK();
+        return MBD_OK;
+    }
     const unsigned blocks = (unsigned)((npts + threads - 1) / threads);
     k_spread_rows<T, false><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
                                                               s->dw64_d.as<double>(), cnt.as<int>(), nullptr);
