@@ -61,6 +61,10 @@ def parse_args():
                          "run as one graph-replayed batch (energies)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mbd_autotune (launch choices by the built-in rules)")
+    ap.add_argument("--choices", default="",
+                    help="apply these launch choices (ld,field_atoms_per_block,fft_tile,spread_tile, as the JSON "
+                         "line's config.autotune reports them) instead of timing them: profiles taken under ncu "
+                         "then run the configuration of a live run")
     ap.add_argument("--cufft", action="store_true",
                     help="also time the FFT convolution (forward 3D FFT, x G, inverse) with cuFFT (torch.fft) "
                          "on the same complex mesh, next to the library's passes")
@@ -323,7 +327,12 @@ def run_ours(args, world, rank, local):
     seed = shard_seed(s.probe_seed, rank, R)
     stream = torch.cuda.Stream()
     sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, quadrature=args.quadrature, stream=stream)
-    tuning = None if args.no_autotune else sysm.autotune(R)
+    if args.choices:
+        vals = [int(v) for v in args.choices.split(",")]
+        tuning = dict(zip(("ld", "field_atoms_per_block", "fft_tile", "spread_tile"), vals))
+        sysm.set_launch_choices(tuning)
+    else:
+        tuning = None if args.no_autotune else sysm.autotune(R)
     info = sysm.info()
     forces = torch.empty((s.n_atoms, 3), dtype=torch.float64, device="cuda")
     energy_t = torch.zeros(1, dtype=torch.float64, device="cuda")
