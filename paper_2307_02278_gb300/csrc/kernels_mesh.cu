@@ -770,6 +770,12 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bo
         FFTArgs<T> c = a;
         c.W = (sizeof(T) == 4 && (inner < 32 || a.K > kWideTileMaxK)) ? 16 : Wmax;
         if (sizeof(T) == 4 && s->tune_fft_w != 0 && s->tune_ld == ld) c.W = inner < 32 ? 16 : s->tune_fft_w;
+        // the pass fused with G does twice the arithmetic per element of the
+        // mesh: on meshes of 97 to 128 points it keeps 32-column tiles (128^3,
+        // 128 probes: 474 -> 462 us per pass on average over the four passes);
+        // longer ones do not (192^3: 818 -> 934 us, the tile's shared memory
+        // leaves too few blocks per SM)
+        if (sizeof(T) == 4 && fused && a.K > kWideTileMaxK && a.K <= 128 && inner >= 32) c.W = 32;
         const int r = launch_fft_ct_sized<T>(c, fused, (unsigned)((size_t)outer * ((inner + c.W - 1) / c.W)),
                                              s->stream);
         if (r == 0) {
