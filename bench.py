@@ -1,12 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the SPME stochastic-Lanczos MBD hot path on GB300.
 
-One step = one mbd_energy_forces call on the 3000-atom water-like box (1000
-molecules, L = 58.66 bohr, mesh 64^3, spline order 6, 64 probes x 50 Lanczos
-steps): probe generation, the Lanczos recurrence with the SPME operator
-(spread, FFT convolution, gather + real space + self), the tridiagonal
-quadrature and the force estimator.  The operator runs in FP32 and the
-Lanczos layer in FP64 (the mixed path); the plain FP64 path is timed beside it.
+One step = one mbd_energy_forces call on the 100,002-atom water-like box
+(33,334 molecules, L = 188.8 bohr, mesh 192^3, spline order 6, Ewald beta 0.30
+bohr^-1, r_cut 12 bohr, 64 probes x 60 Lanczos steps): probe generation, the
+Lanczos recurrence with the SPME operator (spread, FFT convolution, gather +
+real space + self), the tridiagonal quadrature and the force estimator.  The
+operator runs in FP32 and the Lanczos layer in FP64 (the mixed path); the
+plain FP64 path is timed beside it.  The 3000- and 24,000-atom boxes are timed
+too and reported under "other_workloads".
 
 Metric: probe-matvecs/s = R m / step time (whole job over all ranks).  The
 timed region carries CUDA events around each step only; the per-stage table
@@ -36,14 +38,15 @@ if ROOT not in sys.path:
 
 METRIC = "probe-matvecs/s and ms per MBD energy+forces at 1 GB300; frac of HBM roofline"
 UNIT = "probe-matvecs/s"
-WORKLOAD = 2        # the 3000-atom water box
 WORKLOADS = {"water3000": 2, "water24000": 3, "water100002": 5}
+DEFAULT_WORKLOAD = "water100002"
+OTHER_WORKLOADS = ("water3000", "water24000")
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -52,22 +55,24 @@ def parse_args():
                          "or the QL eigendecomposition in FP64 or double-float)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="water3000", choices=list(WORKLOADS) + ["batch64"],
-                    help="water3000 (default, the bench line): 3000-atom water box, mesh 64^3, 64 x 50; "
-                         "water24000: 24000 atoms, mesh 128^3, 128 x 60; water100002: 100002 atoms, mesh 192^3, "
-                         "64 x 60; batch64: the 64 uneven random boxes (200-20000 atoms, 32 probes x 40 steps) "
-                         "run as one graph-replayed batch (energies)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS) + ["batch64"],
+                    help="water100002 (default, the bench line): 100002 atoms, mesh 192^3, 64 x 60; "
+                         "water24000: 24000 atoms, mesh 128^3, 128 x 60; water3000: 3000-atom water box, mesh "
+                         "64^3, 64 x 50; batch64: the 64 uneven random boxes (200-20000 atoms, 32 probes x 40 "
+                         "steps) run as one graph-replayed batch (energies)")
+    ap.add_argument("--other-steps", type=int, default=5,
+                    help="timed steps of each other water box reported beside the bench line (0: none)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mbd_autotune (launch choices by the built-in rules)")
     ap.add_argument("--choices", default="",
                     help="apply these launch choices (ld,field_atoms_per_block,fft_tile,spread_tile, as the JSON "
                          "line's config.autotune reports them) instead of timing them: profiles taken under ncu "
                          "then run the configuration of a live run")
-    ap.add_argument("--cufft", action="store_true",
-                    help="also time the FFT convolution (forward 3D FFT, x G, inverse) with cuFFT (torch.fft) "
-                         "on the same complex mesh, next to the library's passes")
+    ap.add_argument("--no-cufft", action="store_true",
+                    help="skip the comparison of the FFT convolution (forward 3D FFT, x G, inverse) with cuFFT "
+                         "(torch.fft) on the same complex mesh")
     ap.add_argument("--study", default="", choices=["", "delta11"],
                     help="delta11: Delta_11 against the mesh for the 14.2 angstrom water and diamond boxes, "
                          "and the parameters mbd_spme_params chooses (JSON lines)")
@@ -157,6 +162,7 @@ def source_hash(files=None) -> str:
 
 # the sources each roofline stage's kernels are built from (a change to any
 # invalidates its recorded DRAM traffic)
+L2_BYTES = 129 * 1000 * 1000     # GB300 L2 (about 129 MB)
 STAGE_SOURCES = {"fft": ["fft.cuh", "fft_sizes_*.cu", "kernels_mesh.cu", "mbd_internal.cuh"]}
 
 
@@ -195,74 +201,73 @@ def stage_bytes(n_atoms, mesh, R, m, s_bytes, n_pairs, p=6):
 
 
 # ---------------------------------------------------------------------------- reference arm
+def oracle_cv_sample(s, n_min: int, seconds: float):
+    """The oracle as it stands on a bounded sample of the workload: products
+    C v of one probe vector with the oracle's SPME operator (the Lanczos step's
+    dominant work), n_min of them at least and more while `seconds` last.
+    Returns (seconds per product, products timed, operator setup seconds)."""
+    import numpy as np
+
+    from oracle.operator import Operator
+
+    t0 = time.perf_counter()
+    op = Operator(s, "spme")
+    setup = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    t = []
+    t_end = time.perf_counter() + seconds
+    while len(t) < n_min or time.perf_counter() < t_end:
+        x = rng.normal(size=(1, 3 * s.n_atoms))
+        t0 = time.perf_counter()
+        op(x)
+        t.append(time.perf_counter() - t0)
+    return float(np.mean(t)), len(t), setup
+
+
+def _oracle_sample_text(s, n, setup):
+    return (f"{n} products C v of one probe with the oracle's SPME operator on {s.name} (FP64 NumPy, 1 thread; "
+            f"operator setup {setup:.1f} s untimed); probe-matvecs/s extrapolated as 1 / (seconds per product): "
+            f"the Lanczos vector updates, the quadrature and the force estimator are not in the sample")
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    import numpy as np
-
-    from oracle.forces import estimator_forces
-    from oracle.operator import Operator
     from workloads.systems import config
 
-    s = config(WORKLOAD)
-    R_s, m_s = 2, 4
-    op = Operator(s, "spme")
-    for _ in range(args.warmup):
-        estimator_forces(op, R_s, m_s, s.probe_seed)
-    t = []
-    for k in range(args.steps):
-        t0 = time.perf_counter()
-        estimator_forces(op, R_s, m_s, s.probe_seed + ((k * R_s) << 32))
-        t.append(time.perf_counter() - t0)
-    per = float(np.mean(t))
-    value = R_s * m_s / per
-    sample = (f"{R_s} probes x {m_s} Lanczos steps + force estimator per step (of {s.n_probes} x {s.n_steps}), "
-              f"FP64 NumPy, 1 thread")
+    s = config(WORKLOADS[args.workload])
+    per_warm, _, setup = oracle_cv_sample(s, max(1, args.warmup), 0.0)
+    per, n, _ = oracle_cv_sample(s, args.steps, 0.0)
+    value = 1.0 / per
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh), "spline_order": s.spline_order,
-                   "n_probes": R_s, "n_steps": m_s},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                   "ewald_beta": s.ewald_beta, "r_cut": s.r_cut, "step": "one oracle product C v (one probe)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": _oracle_sample_text(s, n, setup), "ms_per_cv": per * 1e3},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline_child(seconds: float):
-    """The oracle as it stands, timed on the host on a bounded sample (runs in a
-    child process started with single-thread BLAS/OpenMP settings)."""
-    import numpy as np
-
-    from oracle.forces import estimator_forces
-    from oracle.operator import Operator
+def cpu_baseline_child(seconds: float, workload: str):
+    """The oracle's bounded sample, run in a child process started with
+    single-thread BLAS/OpenMP settings."""
     from workloads.systems import config
 
-    s = config(WORKLOAD)
-    R_s, m_s = 2, 4
-    t_setup = time.perf_counter()
-    op = Operator(s, "spme")
-    t_setup = time.perf_counter() - t_setup
-    t = []
-    t_end = time.perf_counter() + seconds
-    k = 0
-    while time.perf_counter() < t_end or not t:
-        t0 = time.perf_counter()
-        estimator_forces(op, R_s, m_s, s.probe_seed + ((k * R_s) << 32))
-        t.append(time.perf_counter() - t0)
-        k += 1
-    per = float(np.mean(t))
-    print(json.dumps({"value": R_s * m_s / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-                      "sample": f"{len(t)} samples of {R_s} probes x {m_s} Lanczos steps + force estimator on "
-                                f"{s.name} (FP64 NumPy, 1 thread; operator setup {t_setup:.1f} s untimed)"}))
+    s = config(WORKLOADS[workload])
+    per, n, setup = oracle_cv_sample(s, 1, seconds)
+    print(json.dumps({"value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+                      "sample": _oracle_sample_text(s, n, setup), "ms_per_cv": per * 1e3}))
 
 
-def cpu_baseline(seconds: float):
+def cpu_baseline(seconds: float, workload: str):
     env = dict(os.environ, **SINGLE_THREAD_ENV)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", "--cpu-seconds", str(seconds)],
-                       capture_output=True, text=True, env=env, cwd=ROOT)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", "--cpu-seconds", str(seconds),
+                        "--workload", workload], capture_output=True, text=True, env=env, cwd=ROOT)
     try:
         return json.loads(r.stdout.strip().splitlines()[-1])
     except Exception:
@@ -306,6 +311,72 @@ def cufft_comparison(mbd, s, precision, R, stream, reps=10):
     torch.cuda.empty_cache()
     return {"mesh": list(K), "probes": R, "ours_ms": ours_ms, "cufft_ms": float(np.median(ts)),
             "note": "ours: 5 passes (k3, k2, k1 fused with G and its inverse, k2, k3); cuFFT: fftn, x G, ifftn"}
+
+
+def roofline(stages, dom, peak, peak_kind, workload, n_prof, npts_bytes):
+    """Roofline line of the dominant stage: achieved = algorithmic bytes per
+    launch / device time per launch against the measured HBM copy bandwidth,
+    and, when an ncu capture of the current sources gives the stage's DRAM
+    traffic per launch, the same fraction on those measured bytes."""
+    d = stages[dom]
+    ach = d["achieved_gbs"]
+    traffic = dram_traffic(dom, workload)
+    out = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "basis": "algorithmic bytes (the stage's inputs and outputs read or written once)",
+           "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+           "duration_source": f"library per-stage CUDA events on its stream over {n_prof} live steps "
+                              "run right after the timed region",
+           "mesh_bytes": npts_bytes, "mesh_exceeds_l2": npts_bytes > L2_BYTES, "traffic": traffic}
+    if traffic is not None:
+        dram_gbs = traffic / (d["us_per_launch"] * 1e-6) / 1e9
+        out["frac_dram"] = dram_gbs / peak
+        out["achieved_dram_gbs"] = dram_gbs
+    return out
+
+
+def other_workload(mbd, s, args, stream, flush):
+    """A shorter measurement of another water box beside the bench line: the
+    same energy + forces step (autotuned, L2 flushed before each step), its
+    device time per step and, from a second pass with the per-stage events,
+    the microseconds per launch of each stage and the FFT pass's fraction of
+    the HBM copy bandwidth."""
+    import numpy as np
+    import torch
+
+    R, m = s.n_probes, s.n_steps
+    g = mbd.MBDSystem.from_workload(s, precision=args.precision, quadrature=args.quadrature, stream=stream)
+    tuning = None if args.no_autotune else g.autotune(R)
+    forces = torch.empty((s.n_atoms, 3), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        g.energy_forces(R, m, s.probe_seed, forces=forces)
+    ms = []
+    for _ in range(args.other_steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.energy_forces(R, m, s.probe_seed, forces=forces)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    g.profile_enable(timing=True)
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        g.energy_forces(R, m, s.probe_seed, forces=forces)
+    prof = g.profile_read()
+    info = g.info()
+    g.close()
+    t = float(np.mean(ms))
+    s_bytes = 4 if args.precision == "mixed" else 8
+    sb = stage_bytes(s.n_atoms, s.mesh, R, m, s_bytes, info["n_pairs"], s.spline_order)
+    us = {k: prof[k][1] * 1e3 / prof[k][0] for k in ("prologue", "spread", "fft", "field") if prof[k][0] > 0}
+    peak, _ = measured_peaks()
+    return {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh), "n_probes": R, "n_steps": m,
+            "steps": args.other_steps, "ms_per_energy_forces": t, "value": R * m / (t * 1e-3), "unit": UNIT,
+            "ns_per_atom_probe_step": t * 1e6 / (s.n_atoms * R * m), "us_per_launch": us,
+            "fft_frac_of_hbm": sb["fft"] / (us["fft"] * 1e-6) / 1e9 / peak if "fft" in us else None,
+            "n_pairs": info["n_pairs"], "autotune": tuning}
 
 
 def run_ours(args, world, rank, local):
@@ -424,11 +495,7 @@ def run_ours(args, world, rank, local):
             stages[name] = d
         dom = max((k for k in stages if k in sb), key=lambda k: stages[k]["ms_total"])
         ach = stages[dom]["achieved_gbs"]
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
-                "duration_source": f"library per-stage CUDA events on its stream over {n_prof} live steps "
-                                   "run right after the timed region",
-                "traffic": dram_traffic(dom, s.name)}
+        roof = roofline(stages, dom, peak, peak_kind, s.name, n_prof, npts_bytes=int(np.prod(s.mesh)) * R * s_bytes)
 
         # ---- end to end through the public API with host buffers
         pos_host = torch.tensor(s.pos, dtype=torch.float64).pin_memory()
@@ -474,12 +541,18 @@ def run_ours(args, world, rank, local):
             s64.close()
 
         cpu = None
-        if not args.no_cpu_baseline and world == 1 and args.workload == "water3000":
-            cpu = cpu_baseline(args.cpu_seconds)
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(args.cpu_seconds, args.workload)
 
         cufft = None
-        if args.cufft:
+        if not args.no_cufft:
             cufft = cufft_comparison(mbd, s, args.precision, R, stream)
+
+        others = {}
+        if args.other_steps > 0:
+            for name in OTHER_WORKLOADS:
+                if name != args.workload:
+                    others[name] = other_workload(mbd, config(WORKLOADS[name]), args, stream, flush)
 
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -506,6 +579,7 @@ def run_ours(args, world, rank, local):
             "fp64_path": fp64,
             "cpu_baseline": cpu,
             "cufft_comparison": cufft,
+            "other_workloads": others,
             "gpu_launches": launches_timed,
             "clocks": clocks,
             "wall_s_timed_region": wall,
@@ -657,7 +731,7 @@ def main():
     args = parse_args()
     world, rank, local = dist_env()
     if args.cpu_child:
-        cpu_baseline_child(args.cpu_seconds)
+        cpu_baseline_child(args.cpu_seconds, args.workload)
         return 0
     if args.impl == "reference":
         return run_reference(args, world, rank)

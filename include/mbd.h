@@ -50,7 +50,8 @@ typedef enum {
     MBD_ERR_CUDA = 3,                   /* a CUDA runtime call or kernel launch failed */
     MBD_ERR_NOT_POSITIVE_DEFINITE = 4,  /* a Ritz value of C was <= 0 (polarisation catastrophe) */
     MBD_ERR_NONFINITE = 5,              /* a NaN or Inf appeared in a result */
-    MBD_ERR_TIMEOUT = 6,                /* a bounded device-side wait ran out */
+    MBD_ERR_TIMEOUT = 6,                /* a bounded device-side wait ran out (reserved: no kernel of
+                                           this build waits on another, so no call returns it) */
     MBD_ERR_UNSUPPORTED = 7,            /* valid request this build does not support */
     MBD_ERR_NO_DEVICE = 8               /* no CUDA device is visible */
 } mbd_status;
@@ -300,7 +301,10 @@ mbd_status mbd_tridiag_functions(int32_t n_probes, int32_t n_steps, const double
  * routine.  Its scratch (about 2.1 MB) is one file-scope device array that every
  * GPU loading the library holds until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) and caches
- * it; make that first call before any stream capture.  Every call shares the
+ * it; make that first call before any stream capture.  The cache lives as long
+ * as the process: after cudaDeviceReset on a device the cached address no
+ * longer names the array, so do not call this entry point on that device
+ * again in the same process.  Every call shares the
  * one array (it keeps the last call's contents; the call clears what must
  * start at zero), so calls that overlap on the GPU, for example on two streams,
  * race: serialise them.  Returns MBD_ERR_INVALID_ARG for R > MBD_NOALLOC_MAX_PROBES
@@ -358,6 +362,14 @@ mbd_status mbd_profile_enable(mbd_system *sys, int32_t enable);
 
 /* Read the counters (synchronises the system's stream). */
 mbd_status mbd_profile_read(mbd_system *sys, mbd_profile *out);
+
+/* ---- failure injection (tests of the error paths; the paper has no counterpart) ----
+ * The n-th device allocation of the library from now on (n = 0: the next one)
+ * reports failure without calling cudaMalloc, exactly as an exhausted device
+ * would: the call that needed it returns MBD_ERR_OOM with its outputs
+ * untouched and the handle still usable.  One allocation fails, then the hook
+ * disarms itself; n < 0 disarms it at once.  Process-wide; always MBD_OK. */
+mbd_status mbd_debug_fail_allocation(int64_t n);
 
 /* Human-readable name of a status code (static storage). */
 const char *mbd_status_string(mbd_status status);

@@ -87,12 +87,16 @@ def bilinear_gradient(sys, p: np.ndarray, q: np.ndarray, mode: str = "spme", pai
     return grad
 
 
-def estimator_forces(op, n_probes: int, n_steps: int, seed: int, first: int = 0):
-    """Stochastic force estimate F = -dE/dR with the probes of the energy estimate."""
+def estimator_forces(op, n_probes: int, n_steps: int, seed: int, first: int = 0, probes=None,
+                     reorth: bool = False):
+    """Stochastic force estimate F = -dE/dR with the probes of the energy estimate.
+    probes: unit start vectors (n_probes, 3N) in place of the Rademacher rule
+    (the pins use the 3N unit vectors, for which the estimate is the exact
+    trace); reorth: full reorthogonalisation of the Lanczos basis."""
     n = op.n
     dim = 3 * n
-    v = normalised_probes(seed, n_probes, dim, first)
-    a, b, length, basis = lanczos(op, v, n_steps, keep_basis=True)
+    v = normalised_probes(seed, n_probes, dim, first) if probes is None else np.asarray(probes, dtype=np.float64)
+    a, b, length, basis = lanczos(op, v, n_steps, reorth=reorth, keep_basis=True)
     w = np.stack([inverse_sqrt_action(a[l], b[l], length[l], basis[l]) for l in range(n_probes)])
     q = np.array([quadrature(a[l], b[l], length[l]) for l in range(n_probes)])
     pg = (w * op.g).reshape(n_probes, n, 3)

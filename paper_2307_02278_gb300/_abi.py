@@ -114,6 +114,7 @@ SIGNATURES = {
     "mbd_get_info": (c_int, [c_void_p, POINTER(Info)]),
     "mbd_profile_enable": (c_int, [c_void_p, c_int32]),
     "mbd_profile_read": (c_int, [c_void_p, POINTER(Profile)]),
+    "mbd_debug_fail_allocation": (c_int, [c_int64]),
     "mbd_status_string": (c_char_p, [c_int]),
     "mbd_last_error": (c_char_p, []),
 }

@@ -4,6 +4,7 @@
 #include "mbd_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -18,10 +19,19 @@ void set_last_error(const char *where, cudaError_t e) {
     g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
 }
 
+// Host-side failure injection (mbd_debug_fail_allocation): when >= 0, the
+// number of device allocations still to succeed before one is reported as
+// failed; -1 when disarmed.
+std::atomic<long long> g_alloc_countdown{-1};
+
 mbd_status DevBuf::ensure(size_t n) {
     if (ptr != nullptr && n <= bytes) return MBD_OK;
     release();
     if (n == 0) n = 16;
+    if (g_alloc_countdown.load() >= 0 && g_alloc_countdown.fetch_sub(1) == 0) {
+        g_last_error = "cudaMalloc: allocation failure injected by mbd_debug_fail_allocation";
+        return MBD_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc(&ptr, n);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -1021,6 +1031,11 @@ const char *mbd_status_string(mbd_status st) {
 }
 
 const char *mbd_last_error(void) { return g_last_error.c_str(); }
+
+mbd_status mbd_debug_fail_allocation(int64_t n) {
+    g_alloc_countdown.store(n < 0 ? -1 : (long long)n);
+    return MBD_OK;
+}
 
 mbd_status mbd_create_system(const mbd_system_desc *desc, void *cuda_stream, mbd_system **out) {
     if (out == nullptr) return MBD_ERR_INVALID_ARG;

@@ -51,10 +51,23 @@ def test_measured_peaks_and_fallback(tmp_path, monkeypatch):
 def test_command_line_defaults(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse_args()
-    assert a.gpus == 1 and a.warmup >= 3 and a.impl == "ours" and a.workload == "water3000"
+    assert a.gpus == 1 and a.warmup >= 3 and a.impl == "ours" and a.workload == "water100002"
     monkeypatch.setattr(sys, "argv", ["bench.py", "--choices", "64,7,16,32", "--impl", "reference"])
     a = bench.parse_args()
     assert [int(v) for v in a.choices.split(",")] == [64, 7, 16, 32] and a.impl == "reference"
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "bogus"])
     with pytest.raises(SystemExit):
         bench.parse_args()
+
+
+def test_roofline_line_labels_its_basis(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    stages = {"fft": {"achieved_gbs": 4000.0, "us_per_launch": 500.0}}
+    r = bench.roofline(stages, "fft", 8000.0, "measured", "w", 20, npts_bytes=2 * 10 ** 9)
+    assert r["frac"] == 0.5 and r["traffic"] is None and "frac_dram" not in r
+    assert r["basis"].startswith("algorithmic") and r["mesh_exceeds_l2"]
+    cur = bench.source_hash(bench.STAGE_SOURCES["fft"])
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic.txt").write_text(f"fft w 2000000000 {cur}\n")
+    r = bench.roofline(stages, "fft", 8000.0, "measured", "w", 20, npts_bytes=10 ** 6)
+    assert abs(r["frac_dram"] - 0.5) < 1e-12 and not r["mesh_exceeds_l2"]

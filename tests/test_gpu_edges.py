@@ -10,6 +10,7 @@ from oracle.dense import dense_energy
 from oracle.forces import estimator_forces
 from oracle.lanczos import slq
 from oracle.operator import Operator
+from _parity import atom_max, close, rel
 from workloads.systems import System, random_system
 
 pytestmark = pytest.mark.gpu
@@ -34,8 +35,6 @@ def _two_atoms():
                   np.array([0.45, 0.5]), np.array([3.3, 3.1]), r_cut=5.4, damp_cut=5.4, mesh=(16, 16, 16))
 
 
-def _rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
 @pytest.mark.parametrize("make", [_one_atom, _two_atoms], ids=["one_atom", "two_atoms"])
@@ -49,7 +48,7 @@ def test_tiny_cells(mbd, make, precision):
     op = Operator(s, "spme")
     x = np.random.default_rng(0).normal(size=(2, 3 * s.n_atoms))
     tol = 1e-11 if precision == "fp64" else 2e-6
-    assert _rel(g.apply_C(torch.tensor(x, device="cuda")).cpu().numpy(), op(x)) < tol
+    close(g.apply_C(torch.tensor(x, device="cuda")).cpu().numpy(), op(x), tol)
     m = 3 * s.n_atoms
     e, det = g.lanczos_energy(4, m, 77, details=True)
     q_ref, _, _, _ = slq(op, 3 * s.n_atoms, 4, m, 77)
@@ -87,7 +86,7 @@ def test_smallest_meshes(mbd, p, K):
     g = mbd.MBDSystem.from_workload(s)
     op = Operator(s, "spme")
     x = np.random.default_rng(1).normal(size=(3, 3 * s.n_atoms))
-    assert _rel(g.apply_C(torch.tensor(x, device="cuda")).cpu().numpy(), op(x)) < 1e-11
+    close(g.apply_C(torch.tensor(x, device="cuda")).cpu().numpy(), op(x), 1e-11)
     e, det = g.lanczos_energy(32, 6, 5, details=True)
     q_ref, _, _, _ = slq(op, 3 * s.n_atoms, 32, 6, 5)
     np.testing.assert_allclose(det["q"], q_ref, rtol=1e-8)

@@ -10,6 +10,7 @@ import torch
 from oracle.forces import estimator_forces
 from oracle.lanczos import lanczos, normalised_probes, slq
 from oracle.operator import Operator
+from _parity import atom_max, close, rel
 from workloads.systems import config
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -28,8 +29,6 @@ def _t(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-def _rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.fixture(scope="module")
@@ -43,9 +42,9 @@ def test_water24000_operator(mbd, water24k):
     x = np.random.default_rng(30).normal(size=(2, 3 * s.n_atoms))
     ref = op(x)
     y64 = mbd.MBDSystem.from_workload(s, precision="fp64").apply_C(_t(x)).cpu().numpy()
-    assert _rel(y64, ref) < 1e-11
+    close(y64, ref, 1e-11)
     y32 = mbd.MBDSystem.from_workload(s, precision="mixed").apply_C(_t(x)).cpu().numpy()
-    assert _rel(y32, ref) < 2e-6
+    close(y32, ref, 2e-6)
 
 
 def test_water24000_lanczos_sampled(mbd, water24k):
@@ -86,9 +85,9 @@ def test_water100k_operator_and_energy(mbd):
     ref = op(x)
     g32 = mbd.MBDSystem.from_workload(s, precision="mixed")
     y = g32.apply_C(_t(x)).cpu().numpy()
-    assert _rel(y, ref) < 2e-6
+    close(y, ref, 2e-6)
     g64 = mbd.MBDSystem.from_workload(s, precision="fp64")
-    assert _rel(g64.apply_C(_t(x)).cpu().numpy(), ref) < 1e-11
+    close(g64.apply_C(_t(x)).cpu().numpy(), ref, 1e-11)
     e32, d32 = g32.lanczos_energy(s.n_probes, s.n_steps, s.probe_seed, details=True)
     e64 = g64.lanczos_energy(s.n_probes, s.n_steps, s.probe_seed)
     assert abs(e32 - e64) <= 1e-5 * abs(e64)

@@ -16,6 +16,7 @@ from oracle.ewald import apply_T, real_space_matrix, self_coefficient
 from oracle.forces import estimator_forces
 from oracle.lanczos import lanczos, normalised_probes, quadrature, slq, slq_energy
 from oracle.operator import Operator
+from _parity import atom_max, close, rel
 from workloads.systems import System, config, random_system
 
 pytestmark = pytest.mark.gpu
@@ -41,8 +42,6 @@ def _skew(mesh=(16, 18, 20)):
     return base.with_(cell=cell, pos=frac @ cell, mesh=mesh, r_cut=5.4, damp_cut=5.4)
 
 
-def _rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
 def _t(x):
@@ -86,7 +85,7 @@ def test_spread_parity(mbd, which):
     d = np.random.default_rng(1).normal(size=(3, s.n_atoms, 3))
     q = g.spread(_t(d), s.mesh).cpu().numpy()
     ref = ospme.spread(s, d)
-    assert _rel(q, ref) < 1e-13
+    close(q, ref, 1e-13, width=1)
 
 
 # ------------------------------------------------------------------ a5-a7 FFT convolution
@@ -97,7 +96,7 @@ def test_convolve_parity(mbd, mesh):
     q = np.random.default_rng(2).normal(size=(5,) + mesh)
     phi = g.convolve(_t(q)).cpu().numpy()
     ref = ospme.convolve(s, q)
-    assert _rel(phi, ref) < 1e-12
+    close(phi, ref, 1e-12, width=1)
 
 
 # ------------------------------------------------------------------ a8-a10 field terms
@@ -112,7 +111,7 @@ def test_field_terms(mbd, which):
     for terms, ref in [(mbd.MBD_TERM_REAL, real), (mbd.MBD_TERM_RECIP, rec), (mbd.MBD_TERM_SELF, slf),
                        (mbd.MBD_TERM_ALL, real + rec + slf)]:
         e = g.field(_t(d), terms).cpu().numpy()
-        assert _rel(e, ref) < 1e-11, terms
+        close(e, ref, 1e-11)
 
 
 # ------------------------------------------------------------------ operator C x
@@ -128,10 +127,10 @@ def test_apply_C_parity(mbd, which):
     g = mbd.MBDSystem.from_workload(s)
     x = np.random.default_rng(4).normal(size=(5, 3 * s.n_atoms))
     y = g.apply_C(_t(x)).cpu().numpy()
-    assert _rel(y, Operator(s, "spme")(x)) < 1e-11
+    close(y, Operator(s, "spme")(x), 1e-11)
     if which == "c1":
-        # spec bound: SPME C x vs direct Ewald at the same split
-        assert _rel(y, Operator(s, "same_split")(x)) <= 1e-5
+        # the operator bound: SPME C x vs direct Ewald at the same split
+        close(y, Operator(s, "same_split")(x), 1e-5, atom_factor=3.0)
 
 
 # ------------------------------------------------------------------ Lanczos energy (a1-a11)
@@ -179,7 +178,7 @@ def test_mixed_precision_energy_c1(mbd):
     assert abs(e32 - e64) <= 1e-5 * abs(e64)
     x = np.random.default_rng(5).normal(size=(4, 3 * s.n_atoms))
     y32 = mbd.MBDSystem.from_workload(s, precision="mixed").apply_C(_t(x)).cpu().numpy()
-    assert _rel(y32, Operator(s, "spme")(x)) < 1e-5
+    close(y32, Operator(s, "spme")(x), 1e-5)
 
 
 # ------------------------------------------------------------------ a12 forces
@@ -223,7 +222,7 @@ def test_update_positions(mbd):
     g.update_positions(pos2)
     x = np.random.default_rng(7).normal(size=(2, 3 * s.n_atoms))
     y = g.apply_C(_t(x)).cpu().numpy()
-    assert _rel(y, Operator(s.with_(pos=pos2), "spme")(x)) < 1e-11
+    close(y, Operator(s.with_(pos=pos2), "spme")(x), 1e-11)
 
 
 def test_polarisation_catastrophe(mbd):
@@ -242,7 +241,7 @@ def test_water3000_sampled(mbd):
     g = mbd.MBDSystem.from_workload(s)
     op = Operator(s, "spme")
     x = np.random.default_rng(8).normal(size=(2, 3 * s.n_atoms))
-    assert _rel(g.apply_C(_t(x)).cpu().numpy(), op(x)) < 1e-11
+    close(g.apply_C(_t(x)).cpu().numpy(), op(x), 1e-11)
     e, det = g.lanczos_energy(s.n_probes, s.n_steps, s.probe_seed, details=True)
     q_ref, _, _, _ = slq(op, 3 * s.n_atoms, 3, s.n_steps, s.probe_seed)
     np.testing.assert_allclose(det["q"][:3], q_ref, rtol=1e-8)
@@ -261,7 +260,7 @@ def test_apply_C_orders_and_widths(mbd, p, nvec, precision):
     x = np.random.default_rng(10 + p + nvec).normal(size=(nvec, 3 * s.n_atoms))
     y = g.apply_C(_t(x)).cpu().numpy()
     tol = 1e-11 if precision == "fp64" else 2e-6
-    assert _rel(y, Operator(s, "spme")(x)) < tol
+    close(y, Operator(s, "spme")(x), tol)
 
 
 @pytest.mark.parametrize("R", [64, 128, 5])

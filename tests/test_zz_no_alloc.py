@@ -75,3 +75,17 @@ def test_noalloc_limits_and_status_reset(lib):
     rc, q = _noalloc(lib, a, b)
     assert rc == 0
     np.testing.assert_allclose(q, _allocating(lib, a, b), rtol=1e-13, atol=0)
+
+
+def test_noalloc_many_probes_and_early_zero_coupling(lib):
+    """R = 300 probes spans three blocks of the preparation kernel; some rows
+    carry a zero coupling mid-way (the tridiagonal ends there), as a Lanczos
+    breakdown leaves them.  Same quadratures as the allocating entry point, on
+    two calls in a row."""
+    a, b = _tridiagonals(300, 24, 14)
+    for r, k in [(0, 3), (7, 11), (150, 1), (299, 20)]:
+        b[r, k] = 0.0
+    for _ in range(2):
+        rc, q = _noalloc(lib, a, b)
+        assert rc == 0
+        np.testing.assert_allclose(q, _allocating(lib, a, b), rtol=1e-13, atol=0)
