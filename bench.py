@@ -62,6 +62,11 @@ def parse_args():
                          "water24000: 24000 atoms, mesh 128^3, 128 x 60; water3000: 3000-atom water box, mesh "
                          "64^3, 64 x 50; batch64: the 64 uneven random boxes (200-20000 atoms, 32 probes x 40 "
                          "steps) run as one graph-replayed batch (energies)")
+    ap.add_argument("--energy-only", action="store_true",
+                    help="time mbd_lanczos_energy instead of mbd_energy_forces (small cases for ncu captures)")
+    ap.add_argument("--lanczos-steps", type=int, default=0,
+                    help="Lanczos steps m per call instead of the workload's (0: the workload's; small cases "
+                         "for ncu captures)")
     ap.add_argument("--other-steps", type=int, default=5,
                     help="timed steps of each other water box reported beside the bench line (0: none)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -394,7 +399,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2307_02278_gb300.parallel import reduce_estimates, shard_seed
     s = config(WORKLOADS[args.workload])
-    R, m = s.n_probes, s.n_steps
+    R, m = s.n_probes, (args.lanczos_steps if args.lanczos_steps > 0 else s.n_steps)
     seed = shard_seed(s.probe_seed, rank, R)
     stream = torch.cuda.Stream()
     sysm = mbd.MBDSystem.from_workload(s, precision=args.precision, quadrature=args.quadrature, stream=stream)
@@ -410,6 +415,8 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step(system, seed_k):
+        if args.energy_only:
+            return system.lanczos_energy(R, m, seed_k)
         e, _ = system.energy_forces(R, m, seed_k, forces=forces)
         if world > 1:
             with torch.cuda.stream(stream):
@@ -510,10 +517,12 @@ def run_ours(args, world, rank, local):
             f_host.copy_(forces, non_blocking=True)
             torch.cuda.synchronize()
             t_e2e.append(time.perf_counter() - t0)
-        e2e_s = float(np.median(t_e2e))
-        e2e = {"value": world * R * m / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
-               "h2d_bytes_per_step": 3 * 8 * s.n_atoms, "d2h_bytes_per_step": 3 * 8 * s.n_atoms + 8,
-               "includes": "update_positions (H2D, neighbour list, splines, pair tensors) + energy_forces + D2H"}
+        e2e = None
+        if t_e2e:
+            e2e_s = float(np.median(t_e2e))
+            e2e = {"value": world * R * m / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                   "h2d_bytes_per_step": 3 * 8 * s.n_atoms, "d2h_bytes_per_step": 3 * 8 * s.n_atoms + 8,
+                   "includes": "update_positions (H2D, neighbour list, splines, pair tensors) + energy_forces + D2H"}
 
         # ---- plain FP64 path on the same workload
         fp64 = None
@@ -560,11 +569,14 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None,
             "dtype": "f32 operator / f64 lanczos" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh),
+            "config": {"workload": s.name + ("" if m == s.n_steps else f"_m{m}"), "n_atoms": s.n_atoms,
+                       "mesh": list(s.mesh),
                        "spline_order": s.spline_order, "n_probes_per_gpu": R, "n_steps": m,
                        "precision": args.precision, "quadrature": args.quadrature, "ewald_beta": s.ewald_beta,
                        "r_cut": s.r_cut,
-                       "n_pairs": info["n_pairs"], "step": "mbd_energy_forces (energy + forces)",
+                       "n_pairs": info["n_pairs"],
+                       "step": "mbd_lanczos_energy (energy)" if args.energy_only
+                       else "mbd_energy_forces (energy + forces)",
                        "autotune": tuning,
                        "l2": "flushed before every timed step (512 MB write, outside the events)",
                        "parallelism": f"probes sharded over {world} GPU(s)"},

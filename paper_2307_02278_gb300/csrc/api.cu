@@ -1325,6 +1325,11 @@ mbd_status mbd_lanczos_energy_dense(int32_t dim, const double *c_dev, double ome
         // g = 1 so that the prologue's d output is y* itself (unused by the dense operator)
         std::vector<double> ones((size_t)dim / 3 + 1, 1.0);
         MBD_CUDA_TRY(cudaMemcpy(s->g_d.ptr, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice));
+        // fresh allocations hold whatever the allocator hands back: clear the
+        // coefficients and the status word as enqueue_lanczos does
+        MBD_CUDA_TRY(cudaMemsetAsync(s->a.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
+        MBD_CUDA_TRY(cudaMemsetAsync(s->b.ptr, 0, sizeof(double) * (size_t)m * z.ld, s->stream));
+        MBD_CUDA_TRY(cudaMemsetAsync(s->status.ptr, 0, sizeof(int) * 4, s->stream));
         for (int k = 0; k < m; ++k) {
             MBD_TRY(launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, dim, s->g_d.as<double>(), s->f64.d.ptr, 8,
                                       z.nblk));

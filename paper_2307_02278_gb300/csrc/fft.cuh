@@ -33,6 +33,11 @@ template <class T>
 int launch_sf3_sized(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *row,
                      const SpreadRec<T> *rec, const typename Cplx<T>::type *tw, cudaStream_t st);
 bool fft_ct_size(int K);
+//   The same fused pass with spreading by pencil records (spline order 6):
+//   W = 32 or 16 for float, 16 for double.
+template <class T>
+int launch_spp_sized(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *prow,
+                     const PencilRec<T> *prec, const T *k3w, const typename Cplx<T>::type *tw, cudaStream_t st);
 
 // Sizes with a compile-time pass and their radices (first stage first), in
 // groups of one translation unit each.
@@ -66,6 +71,18 @@ MBD_SF3_DECL(3)
 MBD_SF3_DECL(4)
 MBD_SF3_DECL(5)
 #undef MBD_SF3_DECL
+#define MBD_SPP_DECL(g)                                                                                          \
+    template <class T>                                                                                           \
+    int launch_spp_group##g(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *prow, \
+                            const PencilRec<T> *prec, const T *k3w, const typename Cplx<T>::type *tw,            \
+                            cudaStream_t st);
+MBD_SPP_DECL(0)
+MBD_SPP_DECL(1)
+MBD_SPP_DECL(2)
+MBD_SPP_DECL(3)
+MBD_SPP_DECL(4)
+MBD_SPP_DECL(5)
+#undef MBD_SPP_DECL
 
 namespace {
 
@@ -541,6 +558,146 @@ int sf3_size(int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const in
     return -1;
 }
 
+// Spreading by pencil records (PencilRec, spline order P) fused with the
+// forward FFT along k3: a block owns one (k1, k2) pencil and W complex
+// probe-pair columns; lane l holds the PPL = 2W / 32 probes 2 c0 + l PPL ...
+// Warp w owns the rows [w K / NW, (w + 1) K / NW) of the pencil.  It walks the
+// records of the points (k1, k2, top3) for top3 from its first row to its
+// last row + P - 2 (mod K) in CSR order, which is the order of top3, and keeps
+// the P rows top3 - P + 1 .. top3 that a record of top3 reaches in registers:
+// each record adds M3(t3) (e0 . d_j) + M3'(t3) (e1 . d_j) to row top3 - t3.
+// When top3 moves past a row's last contributor the row is complete and goes
+// to the shared tile (rows outside the warp's range belong to a neighbour and
+// are dropped), so every row is a sum in a fixed order.  The next record is
+// loaded one iteration ahead.  The block then transforms the tile along k3 and
+// writes it once.  Probes >= R are zero.
+template <class T, int K, int W, int NT, int P, int... RS>
+__global__ void __launch_bounds__(NT) k_spread_pencil_fft3(const T *__restrict__ d,
+                                                           typename Cplx<T>::type *__restrict__ mesh, int R, int ld,
+                                                           const int *__restrict__ prow,
+                                                           const PencilRec<T> *__restrict__ prec,
+                                                           const T *__restrict__ k3w,
+                                                           const typename Cplx<T>::type *__restrict__ twg) {
+    using C = typename Cplx<T>::type;
+    constexpr int PPL = 2 * W / 32;           // probes per lane
+    static_assert(PPL == 1 || PPL == 2, "tiles of 16 or 32 complex columns");
+    static_assert(P <= 8, "k3 stencils hold at most 8 points");
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_spp[];
+    C *buf0 = reinterpret_cast<C *>(smem_spp);
+    C *buf1 = buf0 + K * W;
+    C *tw = buf1 + K * W;
+    int *rp = reinterpret_cast<int *>(tw + K);   // [K + 1] record starts of the pencil's points
+    pdl_launch_dependents();
+    const int V = ld / 2;
+    const int ncb = V / W;
+    const size_t pencil = blockIdx.x / ncb;      // k1 * K2 + k2
+    const int c0 = (int)(blockIdx.x % ncb) * W;
+    for (int i = threadIdx.x; i < K; i += NT) tw[i] = twg[i];   // set up once per system
+    for (int i = threadIdx.x; i <= K; i += NT) rp[i] = prow[pencil * K + i];
+    pdl_wait();
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = warp * K / NW, r1 = (warp + 1) * K / NW;
+    const int pr0 = 2 * c0 + lane * PPL;        // first probe of the lane
+    T msk[PPL];
+#pragma unroll
+    for (int e = 0; e < PPL; ++e) msk[e] = pr0 + e < R ? T(1) : T(0);
+    T *tile = reinterpret_cast<T *>(buf0);      // [K][2W] reals
+    T acc[P][PPL];                              // acc[j]: row cur - P + 1 + j
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+#pragma unroll
+        for (int e = 0; e < PPL; ++e) acc[j][e] = T(0);
+    int cur = r0;
+    // row cur - P + 1 is complete: to the tile if it is this warp's, then shift the window
+#define MBD_SPP_FLUSH_ADVANCE()                                                                     \
+    do {                                                                                            \
+        const int row_ = cur - P + 1;                                                               \
+        if (row_ >= r0) {                                                                           \
+            _Pragma("unroll") for (int e = 0; e < PPL; ++e) tile[row_ * 2 * W + lane * PPL + e] =   \
+                acc[0][e] * msk[e];                                                                 \
+        }                                                                                           \
+        _Pragma("unroll") for (int j = 0; j < P - 1; ++j)                                          \
+            _Pragma("unroll") for (int e = 0; e < PPL; ++e) acc[j][e] = acc[j + 1][e];             \
+        _Pragma("unroll") for (int e = 0; e < PPL; ++e) acc[P - 1][e] = T(0);                      \
+        ++cur;                                                                                      \
+    } while (0)
+    // the last (unwrapped) top3 reaching row r1 - 1; beyond K it wraps to 0..
+    const int last = r1 + P - 2;
+    for (int seg = 0; seg < 2; ++seg) {
+        const int t_lo = seg == 0 ? r0 : K, t_hi = seg == 0 ? min(last, K - 1) : last;   // top3 (+ K) range
+        if (t_hi < t_lo) continue;
+        int q = rp[t_lo - seg * K];
+        const int qe = rp[t_hi - seg * K + 1];
+        PencilRec<T> rc{};
+        if (q < qe) rc = prec[q];
+        for (; q < qe; ++q) {
+            PencilRec<T> rn = rc;
+            if (q + 1 < qe) rn = prec[q + 1];
+            T x[PPL], y[PPL], z[PPL];
+            const T *dj = d + (size_t)(3 * rc.atom) * ld + pr0;
+            vload<T, PPL>(dj, x);
+            vload<T, PPL>(dj + ld, y);
+            vload<T, PPL>(dj + 2 * (size_t)ld, z);
+            T m3[P], n3[P];
+            const T *kw = k3w + (size_t)rc.atom * 16;
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                m3[t] = kw[t];
+                n3[t] = kw[8 + t];
+            }
+            // complete the rows no record of this top3 or later reaches
+            const int tcur = rc.top3 + seg * K;
+            while (cur < tcur) MBD_SPP_FLUSH_ADVANCE();
+#pragma unroll
+            for (int e = 0; e < PPL; ++e) {
+                const T u = rc.e0[0] * x[e] + rc.e0[1] * y[e] + rc.e0[2] * z[e];
+                const T v = rc.e1[0] * x[e] + rc.e1[1] * y[e] + rc.e1[2] * z[e];
+#pragma unroll
+                for (int t = 0; t < P; ++t) acc[P - 1 - t][e] += m3[t] * u + n3[t] * v;
+            }
+            rc = rn;
+        }
+    }
+    while (cur <= last) MBD_SPP_FLUSH_ADVANCE();
+#undef MBD_SPP_FLUSH_ADVANCE
+    __syncthreads();
+    C *base = mesh + pencil * (size_t)K * V + c0;
+    ct_pipe<T, C, K, W, NT, 1, 1, false, true, false, RS...>(base, base, (size_t)V, W, buf0, buf1, tw, -1,
+                                                              (const T *)nullptr, 0, c0, V);
+}
+
+template <class T, int K, int W, int... RS>
+int launch_spp(const T *d, T *mesh, int R, int ld, int K1, int K2, const int *prow, const PencilRec<T> *prec,
+               const T *k3w, const typename Cplx<T>::type *tw, cudaStream_t st) {
+    using C = typename Cplx<T>::type;
+    constexpr int NT = ct_threads<K, W, RS...>();
+    static_assert(NT % 32 == 0 && K >= 2 * 6, "whole warps; K >= 2p");
+    const size_t smem = sizeof(C) * (2 * (size_t)K * W + K) + sizeof(int) * (K + 1);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_spread_pencil_fft3<T, K, W, NT, 6, RS...>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    const int V = ld / 2;
+    const unsigned grid = (unsigned)((size_t)K1 * K2 * (V / W));
+    launch_pdl(true, k_spread_pencil_fft3<T, K, W, NT, 6, RS...>, dim3(grid), dim3(NT), smem, st, d,
+               reinterpret_cast<C *>(mesh), R, ld, prow, prec, k3w, tw);
+    return 1;
+}
+
+template <class T, int K, int... RS>
+int spp_size(int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *prow, const PencilRec<T> *prec,
+             const T *k3w, const typename Cplx<T>::type *tw, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (W == 32) return launch_spp<T, K, 32, RS...>(d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st);
+        if (W == 16) return launch_spp<T, K, 16, RS...>(d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st);
+    } else {
+        if (W == 16) return launch_spp<T, K, 16, RS...>(d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st);
+    }
+    return -1;
+}
+
 }  // namespace
 
 // The translation unit of group g: dispatch over its sizes.
@@ -548,6 +705,8 @@ int sf3_size(int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const in
     case K: return ct_size<T, K, __VA_ARGS__>(a, fused, grid, st);
 #define MBD_SF3_CASE(K, ...) \
     case K: return sf3_size<T, K, __VA_ARGS__>(W, d, mesh, R, ld, K1, K2, row, rec, tw, st);
+#define MBD_SPP_CASE(K, ...) \
+    case K: return spp_size<T, K, __VA_ARGS__>(W, d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st);
 #define MBD_FFT_GROUP_TU(g)                                                                                       \
     template <class T> int launch_fft_ct_group##g(const FFTArgs<T> &a, bool fused, unsigned grid, cudaStream_t st) { \
         switch (a.K) { MBD_FFT_GROUP##g(MBD_CT_CASE) default: return -1; }                                         \
@@ -562,6 +721,17 @@ int sf3_size(int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const in
     template int launch_sf3_group##g<float>(int, int, const float *, float *, int, int, int, int, const int *,     \
                                             const SpreadRec<float> *, const float2 *, cudaStream_t);               \
     template int launch_sf3_group##g<double>(int, int, const double *, double *, int, int, int, int, const int *,  \
-                                             const SpreadRec<double> *, const double2 *, cudaStream_t);
+                                             const SpreadRec<double> *, const double2 *, cudaStream_t);           \
+    template <class T>                                                                                             \
+    int launch_spp_group##g(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *prow,    \
+                            const PencilRec<T> *prec, const T *k3w, const typename Cplx<T>::type *tw,              \
+                            cudaStream_t st) {                                                                     \
+        switch (K3) { MBD_FFT_GROUP##g(MBD_SPP_CASE) default: return -1; }                                         \
+    }                                                                                                              \
+    template int launch_spp_group##g<float>(int, int, const float *, float *, int, int, int, int, const int *,     \
+                                            const PencilRec<float> *, const float *, const float2 *, cudaStream_t); \
+    template int launch_spp_group##g<double>(int, int, const double *, double *, int, int, int, int, const int *,  \
+                                             const PencilRec<double> *, const double *, const double2 *,          \
+                                             cudaStream_t);
 
 }  // namespace mbd

@@ -169,6 +169,75 @@ __global__ void k_spread_rows_brick(Geom g, BinView B, const int *__restrict__ t
     if (!FILL) cnt_or_row[pt] = c;
 }
 
+// Pencil records (PencilRec): a thread per mesh point (k1, k2, k3) finds the
+// atoms whose top stencil point is (k1 + t1, k2 + t2, k3), t1, t2 < p (mod K),
+// in the bricks that hold those tops, visited in a fixed order (candidate
+// bricks in order, atoms of a brick by index), so the records of a point come
+// in a fixed order.  FILL = false counts, FILL = true writes e0 and e1 from
+// the FP64 stencil weights.
+template <class T, bool FILL>
+__global__ void k_pencil_rows(Geom g, BinView B, const int *__restrict__ top, const double *__restrict__ w64,
+                              const double *__restrict__ dw64, int *__restrict__ cnt_or_row,
+                              PencilRec<T> *__restrict__ rec) {
+    const size_t npts = (size_t)g.K1 * g.K2 * g.K3;
+    const size_t pt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pt >= npts) return;
+    const int g3 = (int)(pt % g.K3), g2 = (int)((pt / g.K3) % g.K2), g1 = (int)(pt / ((size_t)g.K2 * g.K3));
+    const int p = g.p;
+    // bricks holding tops in [g1, g1 + p - 1] (and likewise along k2), the one holding k3
+    const int b1 = g1 / B.bs1, b2 = g2 / B.bs2, b3 = g3 / B.bs3;
+    const int n1 = min(B.nb1, (g1 + p - 1) / B.bs1 - b1 + 1);
+    const int n2 = min(B.nb2, (g2 + p - 1) / B.bs2 - b2 + 1);
+    int c = 0;
+    const int base = FILL ? cnt_or_row[pt] : 0;
+    for (int c1 = 0; c1 < n1; ++c1) {
+        const int t1b = (b1 + c1) % B.nb1;
+        for (int c2 = 0; c2 < n2; ++c2) {
+            const int t2b = (b2 + c2) % B.nb2;
+            const int bin = (t1b * B.nb2 + t2b) * B.nb3 + b3;
+            for (int s = B.start[bin]; s < B.start[bin + 1]; ++s) {
+                const int j = B.atoms[s];
+                if (top[3 * j + 2] != g3) continue;
+                int u1 = top[3 * j] - g1;
+                if (u1 < 0) u1 += g.K1;
+                int u2 = top[3 * j + 1] - g2;
+                if (u2 < 0) u2 += g.K2;
+                if (u1 >= p || u2 >= p) continue;
+                if (FILL) {
+                    const double *w = w64 + (size_t)3 * p * j, *dw = dw64 + (size_t)3 * p * j;
+                    const double m1 = w[u1], m2 = w[p + u2], n1v = dw[u1], n2v = dw[p + u2];
+                    const double a = n1v * m2, b = m1 * n2v, cc = m1 * m2;
+                    PencilRec<T> r;
+#pragma unroll
+                    for (int al = 0; al < 3; ++al) {
+                        r.e0[al] = T(g.cmat[al] * a + g.cmat[3 + al] * b);
+                        r.e1[al] = T(g.cmat[6 + al] * cc);
+                    }
+                    r.atom = j;
+                    r.top3 = g3;
+                    rec[base + c] = r;
+                }
+                ++c;
+            }
+        }
+    }
+    if (!FILL) cnt_or_row[pt] = c;
+}
+
+// The k3 stencil of each atom for the pencil spreading: k3w[j][t] = M3(t),
+// k3w[j][8 + t] = M3'(t) (t < p <= 8), zero elsewhere.
+template <class T>
+__global__ void k_pencil_k3w(int N, int p, const double *__restrict__ w64, const double *__restrict__ dw64,
+                             T *__restrict__ k3w) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 16 * N) return;
+    const int j = idx / 16, t = idx % 16;
+    const int tt = t & 7;
+    double v = 0.0;
+    if (tt < p) v = (t < 8 ? w64 : dw64)[(size_t)(3 * j + 2) * p + tt];
+    k3w[idx] = T(v);
+}
+
 // Exclusive scan of n counts (blocks of 4096), the block sums, and the fix-up.
 __global__ void __launch_bounds__(1024) k_scan_block(const int *__restrict__ in, int *__restrict__ out,
                                                      int *__restrict__ bsum, int n) {
@@ -603,6 +672,8 @@ mbd_status launch_exclusive_scan(const int *in, int *out, int n, DevBuf &bsum, c
     return MBD_OK;
 }
 
+template <class T> mbd_status build_pencil_records(mbd_system *s);
+
 template <class T> mbd_status build_spread_matrix(mbd_system *s) {
     PrecData<T> &P = prec<T>(s);
     const Geom g = geom_of(s);
@@ -631,7 +702,7 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s) {
                                                                    s->dw64_d.as<double>(), P.srow.template as<int>(),
                                                                    P.srec.template as<SpreadRec<T>>());
         MBD_LAUNCH_CHECK();
-        return MBD_OK;
+        return s->p == kPencilOrder ? build_pencil_records<T>(s) : MBD_OK;
     }
     const unsigned blocks = (unsigned)((npts + threads - 1) / threads);
     k_spread_rows<T, false><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
@@ -642,6 +713,37 @@ template <class T> mbd_status build_spread_matrix(mbd_system *s) {
                                                              s->dw64_d.as<double>(), P.srow.template as<int>(),
                                                              P.srec.template as<SpreadRec<T>>());
     MBD_LAUNCH_CHECK();
+    return s->p == kPencilOrder ? build_pencil_records<T>(s) : MBD_OK;
+}
+
+// The pencil records of spline order 6 (the order of the fused pencil
+// spreading): counts, CSR starts, records, and the per-atom k3 stencils.
+template <class T> mbd_status build_pencil_records(mbd_system *s) {
+    PrecData<T> &P = prec<T>(s);
+    const Geom g = geom_of(s);
+    const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
+    const size_t nnz = (size_t)s->p * s->p * (size_t)s->N;   // each atom covers p^2 pencils (K >= 2p)
+    if (npts >= 0x7fffffffULL || nnz >= 0x7fffffffULL) return MBD_ERR_UNSUPPORTED;
+    MBD_TRY(P.prow.ensure(sizeof(int) * (npts + 1)));
+    MBD_TRY(P.prec.ensure(sizeof(PencilRec<T>) * std::max<size_t>(1, nnz)));
+    MBD_TRY(P.k3w.ensure(sizeof(T) * 16 * std::max(1, s->N)));
+    DevBuf &cnt = s->scan_cnt, &bsum = s->scan_bsum;
+    MBD_TRY(cnt.ensure(sizeof(int) * npts));
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((npts + threads - 1) / threads);
+    k_pencil_rows<T, false><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
+                                                              s->dw64_d.as<double>(), cnt.as<int>(), nullptr);
+    MBD_LAUNCH_CHECK();
+    MBD_TRY(launch_exclusive_scan(cnt.as<int>(), P.prow.template as<int>(), (int)npts, bsum, s->stream));
+    k_pencil_rows<T, true><<<blocks, threads, 0, s->stream>>>(g, s->bins, s->top_d.as<int>(), s->w64_d.as<double>(),
+                                                             s->dw64_d.as<double>(), P.prow.template as<int>(),
+                                                             P.prec.template as<PencilRec<T>>());
+    MBD_LAUNCH_CHECK();
+    if (s->N > 0) {
+        k_pencil_k3w<T><<<(16 * s->N + threads - 1) / threads, threads, 0, s->stream>>>(
+            s->N, s->p, s->w64_d.as<double>(), s->dw64_d.as<double>(), P.k3w.template as<T>());
+        MBD_LAUNCH_CHECK();
+    }
     return MBD_OK;
 }
 
@@ -720,6 +822,18 @@ int launch_sf3_sized(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, 
     return launch_sf3_group5<T>(K3, W, d, mesh, R, ld, K1, K2, row, rec, tw, st);
 }
 
+template <class T>
+int launch_spp_sized(int K3, int W, const T *d, T *mesh, int R, int ld, int K1, int K2, const int *prow,
+                     const PencilRec<T> *prec, const T *k3w, const typename Cplx<T>::type *tw, cudaStream_t st) {
+    int r;
+    if ((r = launch_spp_group0<T>(K3, W, d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st)) >= 0) return r;
+    if ((r = launch_spp_group1<T>(K3, W, d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st)) >= 0) return r;
+    if ((r = launch_spp_group2<T>(K3, W, d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st)) >= 0) return r;
+    if ((r = launch_spp_group3<T>(K3, W, d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st)) >= 0) return r;
+    if ((r = launch_spp_group4<T>(K3, W, d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st)) >= 0) return r;
+    return launch_spp_group5<T>(K3, W, d, mesh, R, ld, K1, K2, prow, prec, k3w, tw, st);
+}
+
 // Spreading fused with the first forward FFT pass when the k3 size has a
 // compile-time pass and the probe-pair columns fill whole tiles.
 bool spread_fft3_supported(const mbd_system *s, int ld, int real_bytes) {
@@ -732,8 +846,13 @@ template <class T> mbd_status launch_spread_fft3(mbd_system *s, const T *d, T *m
     const int W = sf3_width(s, ld / 2, (int)sizeof(T));
     if (W == 0) return MBD_ERR_UNSUPPORTED;
     using C = typename Cplx<T>::type;
-    const int r = launch_sf3_sized<T>(s->K[2], W, d, mesh, R, ld, s->K[0], s->K[1], P.srow.template as<int>(),
-                                      P.srec.template as<SpreadRec<T>>(), P.tw3.template as<C>(), s->stream);
+    // spline order 6: spreading by pencil records; other orders by the point records
+    const int r = s->p == kPencilOrder
+                      ? launch_spp_sized<T>(s->K[2], W, d, mesh, R, ld, s->K[0], s->K[1], P.prow.template as<int>(),
+                                            P.prec.template as<PencilRec<T>>(), P.k3w.template as<T>(),
+                                            P.tw3.template as<C>(), s->stream)
+                      : launch_sf3_sized<T>(s->K[2], W, d, mesh, R, ld, s->K[0], s->K[1], P.srow.template as<int>(),
+                                            P.srec.template as<SpreadRec<T>>(), P.tw3.template as<C>(), s->stream);
     if (r < 0) return MBD_ERR_UNSUPPORTED;
     if (r == 0) {
         set_last_error("fused spreading: shared-memory size", cudaGetLastError());

@@ -220,11 +220,27 @@ template <class T> struct SpreadRec;
 template <> struct __align__(16) SpreadRec<float> { float w0, w1, w2; int atom; };
 template <> struct __align__(16) SpreadRec<double> { double w0, w1, w2; int atom; int pad; };
 
+// One (pencil, atom) record of the factorised spreading: for the pencil
+// (k1, k2) and an atom j whose stencil covers it (t1 = top1 - k1, t2 = top2 - k2
+// mod K), the weights along the pencil are
+//   dW_j/dR_alpha (k1, k2, top3 - t3) = M3(t3) e0_alpha + M3'(t3) e1_alpha,
+//   e0_alpha = C_{0 alpha} M1'(t1) M2(t2) + C_{1 alpha} M1(t1) M2'(t2),
+//   e1_alpha = C_{2 alpha} M1(t1) M2(t2),   C_{beta alpha} = K_beta a*_{beta alpha}.
+// Records are grouped by the mesh point (k1, k2, top3_j) (CSR over points).
+constexpr int kPencilOrder = 6;   // the spline order the pencil spreading is compiled for
+template <class T> struct __align__(16) PencilRec {
+    T e0[3], e1[3];
+    int atom, top3;
+};
+
 template <class T> struct PrecData {
     DevBuf pairA;       // [nnz][6]
     DevBuf pairdA;      // [nnz][18] dA_ab/dr_c (forces)
     DevBuf srow;        // [K^3 + 1] CSR row pointers of the spread matrix
     DevBuf srec;        // [216 N] SpreadRec<T>
+    DevBuf prow;        // [K^3 + 1] CSR over points (k1, k2, top3) of the pencil records (spline order 6)
+    DevBuf prec;        // [36 N] PencilRec<T>
+    DevBuf k3w;         // [N][16] M3(t3) (t3 < p) at 0.., M3'(t3) at 8..
     DevBuf w, dw, d2w;  // [N][3][p]
     DevBuf G;           // [K1K2K3] influence function
     DevBuf tw1, tw2, tw3;   // twiddles [K] complex per dimension
