@@ -187,18 +187,22 @@ def dram_traffic(stage: str, workload: str):
     return None
 
 
-def stage_bytes(n_atoms, mesh, R, m, s_bytes, n_pairs, p=6):
+def stage_bytes(n_atoms, mesh, R, m, s_bytes, n_pairs, p=6, real_clusters=False):
     """Algorithmic HBM bytes per launch of each stage (minimum traffic of the
-    stage's inputs and outputs; every array read or written once)."""
+    stage's inputs and outputs; every array read or written once).  With the
+    real-space clusters the pairs are read by the "real" stage, which writes
+    E_real for the field kernel to read."""
     npts = mesh[0] * mesh[1] * mesh[2]
     rows = 3 * n_atoms
     R2 = 2 * R
+    pairs = n_pairs * (6 * s_bytes + 4)
     return {
         "prologue": rows * R * (4 * 8 + s_bytes),                     # read l, y_{k-1}, y_{k-2}; write y*, d
         "spread": npts * R * s_bytes + rows * R * s_bytes + n_atoms * 3 * p * 2 * s_bytes,
         "fft": 2 * npts * R * s_bytes,                                 # one pass: read + write the mesh
-        "field": (npts * R * s_bytes + rows * R * s_bytes + n_pairs * (6 * s_bytes + 4)
-                  + rows * R * 8 * 3),                                 # mesh, d, pairs, y* in / y, l out
+        "real": 2 * rows * R * s_bytes + pairs,                        # d and the pair tensors in, E_real out
+        "field": (npts * R * s_bytes + rows * R * s_bytes + (rows * R * s_bytes if real_clusters else pairs)
+                  + rows * R * 8 * 3),                                 # mesh, d, E_real or pairs, y* in / y, l out
         "force_spread": npts * R2 * s_bytes + rows * R2 * s_bytes,
         "force_fft": 2 * npts * R2 * s_bytes,
         "force_gather": npts * R2 * s_bytes + rows * R2 * s_bytes + n_pairs * 8,
@@ -374,8 +378,10 @@ def other_workload(mbd, s, args, stream, flush):
     g.close()
     t = float(np.mean(ms))
     s_bytes = 4 if args.precision == "mixed" else 8
-    sb = stage_bytes(s.n_atoms, s.mesh, R, m, s_bytes, info["n_pairs"], s.spline_order)
-    us = {k: prof[k][1] * 1e3 / prof[k][0] for k in ("prologue", "spread", "fft", "field") if prof[k][0] > 0}
+    sb = stage_bytes(s.n_atoms, s.mesh, R, m, s_bytes, info["n_pairs"], s.spline_order,
+                     real_clusters=prof["real"][0] > 0)
+    us = {k: prof[k][1] * 1e3 / prof[k][0] for k in ("prologue", "spread", "fft", "real", "field")
+          if prof[k][0] > 0}
     peak, _ = measured_peaks()
     return {"workload": s.name, "n_atoms": s.n_atoms, "mesh": list(s.mesh), "n_probes": R, "n_steps": m,
             "steps": args.other_steps, "ms_per_energy_forces": t, "value": R * m / (t * 1e-3), "unit": UNIT,
@@ -485,7 +491,8 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         # ---- roofline of the dominant stage
         s_bytes = 4 if args.precision == "mixed" else 8
-        sb = stage_bytes(s.n_atoms, s.mesh, R, m, s_bytes, info["n_pairs"], s.spline_order)
+        sb = stage_bytes(s.n_atoms, s.mesh, R, m, s_bytes, info["n_pairs"], s.spline_order,
+                         real_clusters=prof["real"][0] > 0)
         peak, peak_kind = measured_peaks()
         stages = {}
         stage_names = [k for k in prof if k != "total_launches"]

@@ -232,6 +232,22 @@ mbd_status mbd_batch_get_info(const mbd_batch *batch, mbd_batch_info *info);
 enum { MBD_BASIS_STORE = 0, MBD_BASIS_RECOMPUTE = 1 };
 mbd_status mbd_set_basis_storage(mbd_system *sys, int32_t mode);
 
+/* ---- evaluation of the real-space field (Eq. fld_ewald) ----
+ * MBD_REAL_PAIRS: inside the field kernel, each atom's neighbours split over
+ *   the warps of a block (every neighbour's dipoles loaded once per pair).
+ * MBD_REAL_CLUSTERS: a kernel of its own over clusters of 8 atoms that are
+ *   consecutive in the Morton order of the mesh bricks: a warp loads each
+ *   distinct neighbour (j, image) of the cluster once and applies it to every
+ *   cluster atom that has it, then the field kernel adds the result.
+ * MBD_REAL_AUTO (default): clusters when there are at least four per SM
+ *   (and probe chunk of 64 FP32 or 32 FP64 probes), else pairs.
+ * The two evaluations sum the same pairs in different orders (results agree
+ * to rounding).  MBD_ERR_UNSUPPORTED for MBD_REAL_CLUSTERS when a cluster has
+ * more than 2048 pairs (more than 256 neighbours per atom on average); the
+ * clusters are rebuilt with every geometry. */
+enum { MBD_REAL_AUTO = 0, MBD_REAL_CLUSTERS = 1, MBD_REAL_PAIRS = 2 };
+mbd_status mbd_set_real_space_method(mbd_system *sys, int32_t method);
+
 /* ---- autotuning ----
  * Times the candidate launch choices for this system at n_probes probes on the
  * system's stream and keeps the fastest.  The candidates are the FP32 FFT tile
@@ -346,7 +362,8 @@ enum {
     MBD_STAGE_FORCE_FFT = 7,
     MBD_STAGE_FORCE_GATHER = 8, /* Hessian gather + real-space pair gradient */
     MBD_STAGE_OTHER = 9,        /* layout transposes, setup */
-    MBD_NUM_STAGES = 10
+    MBD_STAGE_REAL = 10,        /* real-space field of the dipoles on atom clusters (Eq. fld_ewald) */
+    MBD_NUM_STAGES = 11
 };
 
 typedef struct {

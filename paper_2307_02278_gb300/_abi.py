@@ -56,9 +56,9 @@ class Info(ctypes.Structure):
     ]
 
 
-NUM_STAGES = 10
+NUM_STAGES = 11
 STAGES = ["prologue", "spread", "fft", "field", "quadrature", "force_prep", "force_spread", "force_fft",
-          "force_gather", "other"]
+          "force_gather", "other", "real"]
 
 
 class Profile(ctypes.Structure):
@@ -115,6 +115,7 @@ SIGNATURES = {
     "mbd_profile_enable": (c_int, [c_void_p, c_int32]),
     "mbd_profile_read": (c_int, [c_void_p, POINTER(Profile)]),
     "mbd_debug_fail_allocation": (c_int, [c_int64]),
+    "mbd_set_real_space_method": (c_int, [c_void_p, c_int32]),
     "mbd_status_string": (c_char_p, [c_int]),
     "mbd_last_error": (c_char_p, []),
 }

@@ -317,10 +317,16 @@ mbd_status build_bins(mbd_system *s) {
     MBD_TRY(launch_bin_atoms(N, s->top_d.as<int>(), B, s->bin_of_d.as<int>(), s->scan_cnt.as<int>(),
                              s->bin_start_d.as<int>(), s->bin_cursor_d.as<int>(), s->bin_atoms_d.as<int>(),
                              s->scan_bsum, s->stream));
-    // the field kernel takes the atoms in the same (spatially sorted) order
-    if (N > 0)
+    // the field kernel and the real-space clusters take the atoms in the
+    // Morton order of their bricks (compact groups of consecutive atoms); a
+    // brick grid too large for the Morton cube keeps the brick-major order
+    const mbd_status mo = launch_morton_order(B, N, s->order_d.as<int>(), s->morton_cnt, s->morton_start,
+                                              s->scan_bsum, s->stream);
+    if (mo == MBD_ERR_UNSUPPORTED && N > 0)
         MBD_CUDA_TRY(cudaMemcpyAsync(s->order_d.ptr, s->bin_atoms_d.ptr, sizeof(int) * N, cudaMemcpyDeviceToDevice,
                                      s->stream));
+    else if (mo != MBD_OK)
+        return mo;
     return MBD_OK;
 }
 
@@ -397,8 +403,18 @@ template <class T> mbd_status setup_geometry(mbd_system *s) {
         MBD_TRY(launch_neighbors(s->ngrid, s->pos_d.as<double>(), s->row_d.as<int>(), s->col_d.as<int>(),
                                  s->shift_d.as<int>(), s->nb_err_d.as<int>(), true, s->nb_cap, s->stream));
         MBD_TRY(launch_pair_tensors<T>(s, s->stream));
-        MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
     }
+    // the clusters of the real-space field, from the final neighbour list
+    s->real_clusters = false;
+    s->n_clusters = (s->N + kClusterSize - 1) / kClusterSize;
+    MBD_TRY(s->cl_err.ensure(sizeof(int)));
+    MBD_CUDA_TRY(cudaMemsetAsync(s->cl_err.ptr, 0, sizeof(int), s->stream));
+    MBD_TRY(launch_cluster_pairs<T>(s, s->order_d.as<int>(), s->n_clusters, s->cl_ecnt, s->cl_pcnt, s->cl_estart,
+                                    s->cl_pstart, s->cl_entries, prec<T>(s).cA, s->cl_err.as<int>(), s->stream));
+    int cerr = 0;
+    MBD_CUDA_TRY(cudaMemcpyAsync(&cerr, s->cl_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->real_clusters = cerr == 0;
     return MBD_OK;
 }
 
@@ -495,6 +511,21 @@ mbd_status create_impl(const mbd_system_desc *d, void *stream, mbd_system **out)
         return fail(MBD_ERR_OOM);
     }
     cudaError_t ce;
+    // the second stream has the highest priority: the FFT passes' large grids
+    // otherwise hold every SM until their last wave, and the real-space blocks
+    // would run only in that tail
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        cudaGetLastError();
+        prio_hi = 0;
+    }
+    if ((ce = cudaStreamCreateWithPriority(&s->stream2, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
+        (ce = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (ce = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+        set_last_error("second stream", ce);
+        cudaGetLastError();
+        return fail(MBD_ERR_CUDA);
+    }
     if ((ce = cudaMemcpyAsync(s->g_d.ptr, g.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) ||
         (ce = cudaMemcpyAsync(s->w2_d.ptr, w2.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) ||
         (ce = cudaMemcpyAsync(s->rvdw_d.ptr, s->rvdw.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
@@ -573,6 +604,7 @@ template <class T> mbd_status ensure_mesh(mbd_system *s, int ld) {
     const size_t npts = (size_t)s->K[0] * s->K[1] * s->K[2];
     MBD_TRY(P.d.ensure(sizeof(T) * 3 * (size_t)s->N * ld));
     MBD_TRY(P.mesh.ensure(sizeof(T) * npts * ld));
+    if (s->real_clusters) MBD_TRY(P.ereal.ensure(sizeof(T) * 3 * (size_t)s->N * ld));
     return MBD_OK;
 }
 
@@ -600,20 +632,32 @@ mbd_status enqueue_steps(mbd_system *s, int R, int m, uint64_t seed, const uint6
     fo.lz = z.v;
     // the fused spread + k3 pass exists for the specialised sizes with whole probe-pair tiles
     const bool fuse3 = spread_fft3_supported(s, z.ld, (int)sizeof(T));
+    // real space on clusters: on the second stream beside the FFT passes,
+    // except while stages are timed (their events live on the system stream)
+    const bool real_cl = real_on_clusters(s, z.ld, (int)sizeof(T));
+    const bool overlap = real_cl && !s->prof.timing && s->stream2 != nullptr;
     for (int k = 0; k < m; ++k) {
         MBD_STAGE(s, MBD_STAGE_PROLOGUE, 1,
                   launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
                                     (int)sizeof(T), z.nblk, seed_dev));
-        if (fuse3) {
-            MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
-                      launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
-            MBD_STAGE(s, MBD_STAGE_FFT, 4, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld, true));
-        } else {
-            MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
-                      launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
-            MBD_STAGE(s, MBD_STAGE_FFT, 5, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld));
+        MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
+                  fuse3 ? launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld)
+                        : launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
+        if (overlap) {
+            MBD_CUDA_TRY(cudaEventRecord(s->ev_fork, s->stream));
+            MBD_CUDA_TRY(cudaStreamWaitEvent(s->stream2, s->ev_fork, 0));
+            MBD_TRY(launch_real_clusters<T>(s, P.d.template as<T>(), P.ereal.template as<T>(), z.ld, s->stream2));
+            prof_end(s, MBD_STAGE_REAL, 1, nullptr);
+            MBD_CUDA_TRY(cudaEventRecord(s->ev_join, s->stream2));
         }
+        MBD_STAGE(s, MBD_STAGE_FFT, fuse3 ? 4 : 5, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld, fuse3));
         fo.k = k;
+        if (overlap) {
+            MBD_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+        } else if (real_cl) {
+            MBD_STAGE(s, MBD_STAGE_REAL, 1,
+                      launch_real_clusters<T>(s, P.d.template as<T>(), P.ereal.template as<T>(), z.ld, s->stream));
+        }
         MBD_STAGE(s, MBD_STAGE_FIELD, 1,
                   launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
         if (k == 0 && v0)
@@ -773,6 +817,9 @@ template <class T> mbd_status apply_impl(mbd_system *s, int nvec, const double *
     fo.xin = xt;
     fo.k = 0;
     std::memset(&fo.lz, 0, sizeof(fo.lz));
+    if (real_on_clusters(s, ld, (int)sizeof(T)) && (terms & MBD_TERM_REAL))
+        MBD_STAGE(s, MBD_STAGE_REAL, 1,
+                  launch_real_clusters<T>(s, P.d.template as<T>(), P.ereal.template as<T>(), ld, s->stream));
     MBD_STAGE(s, MBD_STAGE_FIELD, 1, launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), nvec, ld, fo));
     MBD_STAGE(s, MBD_STAGE_OTHER, 1, launch_from_probe_major(yt, nvec, rows, ld, y, s->stream));
     MBD_CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -919,6 +966,7 @@ template <class T> mbd_status autotune_impl(mbd_system *s, int R, int32_t *out) 
     MBD_CUDA_TRY(cudaMemsetAsync(P.d.ptr, 0, sizeof(T) * rows * ld, s->stream));
     MBD_CUDA_TRY(cudaMemsetAsync(P.mesh.ptr, 0, sizeof(T) * npts * ld, s->stream));
     MBD_CUDA_TRY(cudaMemsetAsync(s->L.ptr, 0, sizeof(double) * rows * ld, s->stream));
+    if (s->real_clusters) MBD_CUDA_TRY(cudaMemsetAsync(P.ereal.ptr, 0, sizeof(T) * rows * ld, s->stream));
     s->tune_ld = ld;
     s->tune_field_apb = s->tune_fft_w = s->tune_sf3_w = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1032,6 +1080,13 @@ const char *mbd_status_string(mbd_status st) {
 
 const char *mbd_last_error(void) { return g_last_error.c_str(); }
 
+mbd_status mbd_set_real_space_method(mbd_system *s, int32_t method) {
+    if (!s || method < MBD_REAL_AUTO || method > MBD_REAL_PAIRS) return MBD_ERR_INVALID_ARG;
+    if (method == MBD_REAL_CLUSTERS && !s->real_clusters) return MBD_ERR_UNSUPPORTED;
+    s->real_method = method;
+    return MBD_OK;
+}
+
 mbd_status mbd_debug_fail_allocation(int64_t n) {
     g_alloc_countdown.store(n < 0 ? -1 : (long long)n);
     return MBD_OK;
@@ -1045,6 +1100,12 @@ mbd_status mbd_create_system(const mbd_system_desc *desc, void *cuda_stream, mbd
 
 void mbd_destroy_system(mbd_system *sys) {
     if (sys == nullptr) return;
+    if (sys->stream2) {
+        cudaStreamSynchronize(sys->stream2);
+        cudaStreamDestroy(sys->stream2);
+    }
+    if (sys->ev_fork) cudaEventDestroy(sys->ev_fork);
+    if (sys->ev_join) cudaEventDestroy(sys->ev_join);
     if (sys->host_scal) cudaFreeHost(sys->host_scal);
     if (sys->host_status) cudaFreeHost(sys->host_status);
     prof_release(sys);

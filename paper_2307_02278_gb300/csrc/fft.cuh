@@ -363,8 +363,10 @@ __global__ void __launch_bounds__(NT) k_fft_ct(FFTArgs<T> a) {
     C *base = a.data + outer * (size_t)K * a.inner + c0;
     const size_t gstride = (size_t)(a.inner / a.V);
     if (FUSED) {
+        // G of this block's slab: G[outer][row][(c0 + col) / V]
+        const T *Gb = a.G + outer * (size_t)K * gstride;
         C *res = ct_pipe<T, C, K, W, NT, CV, 1, true, false, true, RS...>(base, base, a.inner, wc, buf0, buf1, tw,
-                                                                           -1, a.G, gstride, c0, a.V);
+                                                                           -1, Gb, gstride, c0, a.V);
         __syncthreads();
         C *other = (res == buf0) ? buf1 : buf0;
         ct_pipe<T, C, K, W, NT, CV, 1, false, true, false, RS...>(base, base, a.inner, wc, res, other, tw, +1, a.G,

@@ -421,11 +421,12 @@ __global__ void __launch_bounds__(256) k_fft_pass(FFTArgs<T> a) {
     if (FUSED) {
         res = stockham<T, C>(b0, b1, a, tw, -1);
         C *other = (res == b0) ? b1 : b0;
-        // G index: k1 = row, (k2, k3) = (c0 + col) / V
+        // G index: (outer, row, (c0 + col) / V)
+        const T *Gb = a.G + outer * (size_t)a.K * (a.inner / a.V);
         for (int idx = threadIdx.x; idx < a.K * a.W; idx += blockDim.x) {
             const int row = idx / a.W, col = idx - row * a.W;
             if (col < wc) {
-                const T gv = a.G[(size_t)row * (a.inner / a.V) + (c0 + col) / a.V];
+                const T gv = Gb[(size_t)row * (a.inner / a.V) + (c0 + col) / a.V];
                 res[idx].x *= gv;
                 res[idx].y *= gv;
             }
@@ -441,6 +442,104 @@ __global__ void __launch_bounds__(256) k_fft_pass(FFTArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------- real space on clusters
+template <class T> struct RealArgs {
+    const T *d;          // [N][3][ld]
+    T *out;              // [N][3][ld] E_real
+    int ld, N, nclus;
+    const int *order;    // cluster c = atoms order[8c .. 8c + 7]
+    const int *estart;   // [nclus + 1] entry starts
+    const int *pstart;   // [8 nclus + 1] pair starts per (cluster, atom)
+    const int *entries;  // distinct neighbours j of each cluster
+    const RealPair<T> *pairs;
+};
+
+// The real-space field E_real = sum over pairs A(r) d_j (Eq. fld_ewald with
+// the damping correction) on clusters: a block per cluster of 8 atoms and
+// probe chunk (blockIdx.y, 32 PPL probes), warp w for cluster atom w, lanes
+// over PPL consecutive probes.  The block stages the dipoles of the cluster's
+// distinct neighbours in shared memory, kRealCE entries at a time (coalesced
+// 16-byte loads by all threads), so each neighbour's dipoles come from L2
+// once per cluster.  Each warp reads its atom's pairs (entry index and
+// tensor) 32 at a time into shared memory, one per lane, and applies those
+// whose entries are staged, accumulating in registers: no global load waits
+// inside the pair loop.  An atom's field is the sum over its pairs in
+// (j, image) order: deterministic.
+constexpr int kRealCE = 48;
+template <class T, int PPL>
+__global__ void __launch_bounds__(256) k_real_clusters(RealArgs<T> a) {
+    constexpr int NP = 32 * PPL;                   // probes of the block
+    constexpr int U = 16 / (int)sizeof(T);         // values per 16-byte load
+    constexpr int PER_ROW = NP / U;                // 16-byte loads per staged row
+    __shared__ __align__(16) T sd[kRealCE][3][NP];
+    __shared__ RealPair<T> sp[kClusterSize][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x;
+    const int pb = blockIdx.y * NP;
+    const int r0 = pb + lane * PPL;
+    const bool inld = r0 < a.ld;
+    const bool vec = a.ld % U == 0;
+    const int eb = a.estart[c], ee = a.estart[c + 1];
+    const int slot = c * kClusterSize + warp;
+    const int pe = a.pstart[slot + 1];
+    int bbase = a.pstart[slot], bn = 0, bi = 0;    // the warp's batch of pairs [bbase, bbase + bn), next bi
+    T E[3][PPL];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int e = 0; e < PPL; ++e) E[k][e] = T(0);
+    for (int c0 = eb; c0 < ee; c0 += kRealCE) {
+        const int ne = min(kRealCE, ee - c0);
+        __syncthreads();                           // the previous chunk is consumed
+        for (int t = threadIdx.x; t < ne * 3 * PER_ROW; t += blockDim.x) {
+            const int q = t / (3 * PER_ROW), rem = t % (3 * PER_ROW), k = rem / PER_ROW, u = rem % PER_ROW;
+            const T *src = a.d + (size_t)(3 * a.entries[c0 + q] + k) * a.ld + pb + u * U;
+            T *dst = &sd[q][k][u * U];
+            if (vec && pb + u * U + U <= a.ld) {
+                *reinterpret_cast<float4 *>(dst) = *reinterpret_cast<const float4 *>(src);
+            } else {
+#pragma unroll
+                for (int v = 0; v < U; ++v) dst[v] = pb + u * U + v < a.ld ? src[v] : T(0);
+            }
+        }
+        __syncthreads();
+        const int lo = c0 - eb, lim = lo + ne;     // entries staged: [lo, lim)
+        for (;;) {
+            if (bi == bn) {                        // the next 32 pairs of this atom
+                bbase += bn;
+                if (bbase >= pe) break;
+                bn = min(32, pe - bbase);
+                bi = 0;
+                __syncwarp();
+                if (lane < bn) sp[warp][lane] = a.pairs[bbase + lane];
+                __syncwarp();
+            }
+            const RealPair<T> cur = sp[warp][bi];
+            if (cur.e >= lim) break;
+            ++bi;
+            const int q = cur.e - lo;
+            T x[PPL], y[PPL], z[PPL];
+#pragma unroll
+            for (int e = 0; e < PPL; ++e) {
+                x[e] = sd[q][0][lane * PPL + e];
+                y[e] = sd[q][1][lane * PPL + e];
+                z[e] = sd[q][2][lane * PPL + e];
+            }
+#pragma unroll
+            for (int e = 0; e < PPL; ++e) {
+                E[0][e] += cur.a[0] * x[e] + cur.a[1] * y[e] + cur.a[2] * z[e];
+                E[1][e] += cur.a[1] * x[e] + cur.a[3] * y[e] + cur.a[4] * z[e];
+                E[2][e] += cur.a[2] * x[e] + cur.a[4] * y[e] + cur.a[5] * z[e];
+            }
+        }
+    }
+    const int idx = c * kClusterSize + warp;
+    if (!inld || idx >= a.N) return;
+    const int i = a.order[idx];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vstore<T, PPL>(a.out + (size_t)(3 * i + k) * a.ld + r0, E[k]);
+}
+
 // ---------------------------------------------------------------- field
 template <class T> struct FieldArgs {
     const T *d;          // [N][3][ld]
@@ -453,6 +552,7 @@ template <class T> struct FieldArgs {
     const double *g_at;  // [N] w sqrt(alpha)
     const double *w2;    // [N] w^2
     double self_coef;
+    const T *ereal;      // when set: the real-space field from k_real_clusters [N][3][ld]
     FieldOut<T> o;
 };
 
@@ -538,7 +638,21 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
                     E2[v] += m02 * f0[v] + m12 * f1[v] + m22 * f2[v];
                 }
             }
-            if (a.o.terms & MBD_TERM_REAL) {
+            if ((a.o.terms & MBD_TERM_REAL) && a.ereal != nullptr) {
+                if (warp == kWarps - 1) {
+                    T x[VEC], y[VEC], z[VEC];
+                    const T *ei = a.ereal + (size_t)(3 * i) * a.ld + r0;
+                    vload<T, VEC>(ei, x);
+                    vload<T, VEC>(ei + a.ld, y);
+                    vload<T, VEC>(ei + 2 * (size_t)a.ld, z);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        E0[v] += x[v];
+                        E1[v] += y[v];
+                        E2[v] += z[v];
+                    }
+                }
+            } else if (a.o.terms & MBD_TERM_REAL) {
                 const int nb1 = a.pr.row[i + 1];
                 constexpr int B4 = 4;
                 for (int nb = a.pr.row[i] + warp; nb < nb1; nb += B4 * kWarps) {
@@ -944,6 +1058,7 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     a.g_at = s->g_d.as<double>();
     a.w2 = s->w2_d.as<double>();
     a.self_coef = -4.0 * s->ewald_beta * s->ewald_beta * s->ewald_beta / (3.0 * 1.77245385090551602730);
+    a.ereal = real_on_clusters(s, ld, (int)sizeof(T)) ? P.ereal.template as<T>() : nullptr;
     a.o = o;
     const int vec = field_vec(ld, (int)sizeof(T));
     const int apb = field_apb(s, ld);
@@ -962,6 +1077,41 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
         else MBD_FIELD_LAUNCH(1, 0);
     }
 #undef MBD_FIELD_LAUNCH
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+
+// The real-space field runs on the clusters when they were built and there
+// are enough of them for four blocks per SM (a block per cluster and probe
+// chunk); smaller systems keep the pair loop of the field kernel, whose warps
+// split the neighbours of one atom.
+bool real_on_clusters(const mbd_system *s, int ld, int real_bytes) {
+    if (!s->real_clusters || s->real_method == MBD_REAL_PAIRS) return false;
+    if (s->real_method == MBD_REAL_CLUSTERS) return true;
+    const int ppl = real_bytes == 4 ? 2 : 1;
+    const long long chunks = (ld + 32 * ppl - 1) / (32 * ppl);
+    return (long long)s->n_clusters * chunks >= 4LL * std::max(1, s->num_sms);
+}
+
+// E_real of every atom from the clusters (the caller runs this before
+// launch_field whenever real_on_clusters holds and the real-space term is wanted).
+template <class T> mbd_status launch_real_clusters(mbd_system *s, const T *d, T *ereal, int ld, cudaStream_t st) {
+    PrecData<T> &P = prec<T>(s);
+    RealArgs<T> a;
+    a.d = d;
+    a.out = ereal;
+    a.ld = ld;
+    a.N = s->N;
+    a.nclus = s->n_clusters;
+    a.order = s->order_d.as<int>();
+    a.estart = s->cl_estart.as<int>();
+    a.pstart = s->cl_pstart.as<int>();
+    a.entries = s->cl_entries.as<int>();
+    a.pairs = P.cA.template as<RealPair<T>>();
+    if (a.nclus == 0) return MBD_OK;
+    constexpr int ppl = sizeof(T) == 4 ? 2 : 1;
+    dim3 grid((unsigned)a.nclus, (unsigned)((ld + 32 * ppl - 1) / (32 * ppl)));
+    k_real_clusters<T, ppl><<<grid, 32 * kClusterSize, 0, st>>>(a);
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }
@@ -1033,5 +1183,7 @@ template mbd_status launch_field<double>(mbd_system *, const double *, const dou
                                          const FieldOut<double> &);
 template mbd_status launch_field<float>(mbd_system *, const float *, const float *, int, int,
                                         const FieldOut<float> &);
+template mbd_status launch_real_clusters<double>(mbd_system *, const double *, double *, int, cudaStream_t);
+template mbd_status launch_real_clusters<float>(mbd_system *, const float *, float *, int, cudaStream_t);
 
 }  // namespace mbd

@@ -384,7 +384,233 @@ __global__ void k_bin_sort(int nbins, const int *__restrict__ start, int *__rest
         atoms[r + 1] = v;
     }
 }
+
+// ---------------------------------------------------------------- Morton order of the bricks
+__device__ __forceinline__ unsigned morton_spread3(unsigned v) {   // bits b -> 3b
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__device__ __forceinline__ unsigned morton_compact3(unsigned v) {  // 3b -> b
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x3ffu;
+    return v;
+}
+// cnt[m] = atoms of the brick at Morton index m of an M^3 cube (0 outside the brick grid)
+__global__ void k_morton_count(unsigned mtotal, BinView B, int *__restrict__ cnt) {
+    const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= mtotal) return;
+    const int b1 = (int)morton_compact3(m >> 2), b2 = (int)morton_compact3(m >> 1), b3 = (int)morton_compact3(m);
+    int c = 0;
+    if (b1 < B.nb1 && b2 < B.nb2 && b3 < B.nb3) {
+        const int bin = (b1 * B.nb2 + b2) * B.nb3 + b3;
+        c = B.start[bin + 1] - B.start[bin];
+    }
+    cnt[m] = c;
+}
+__global__ void k_morton_fill(unsigned mtotal, BinView B, const int *__restrict__ start, int *__restrict__ order) {
+    const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= mtotal) return;
+    const int b1 = (int)morton_compact3(m >> 2), b2 = (int)morton_compact3(m >> 1), b3 = (int)morton_compact3(m);
+    if (b1 >= B.nb1 || b2 >= B.nb2 || b3 >= B.nb3) return;
+    const int bin = (b1 * B.nb2 + b2) * B.nb3 + b3;
+    const int o = start[m];
+    for (int s = B.start[bin]; s < B.start[bin + 1]; ++s) order[o + (s - B.start[bin])] = B.atoms[s];
+}
+
+// ---------------------------------------------------------------- clusters of the real-space field
+// Cluster c is the atoms order[8c .. 8c + 7] (consecutive in the Morton order
+// of the bricks, so close in space).  Its entries are the distinct neighbours
+// j of its atoms (over all images), in increasing j; its pairs are grouped by
+// the cluster atom il (pair starts per (c, il)) and, within an atom, ordered
+// by (j, image), each carrying the index of its entry and its pair tensor.
+// A block per cluster sorts the cluster's pairs in shared memory (bitonic,
+// keys (j, image, il)); COUNT = true counts entries and pairs, COUNT = false
+// writes them at the scanned starts.
+__device__ __forceinline__ void bitonic_sort_smem(unsigned long long *key, int n) {
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int ij = i ^ j;
+                if (ij > i) {
+                    const unsigned long long a = key[i], b = key[ij];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        key[i] = b;
+                        key[ij] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <class T, bool COUNT>
+__global__ void __launch_bounds__(256) k_cluster_pairs(int N, int nclus, const int *__restrict__ order,
+                                                       const int *__restrict__ row, const int *__restrict__ col,
+                                                       const int *__restrict__ shift, const double *__restrict__ pos,
+                                                       const double *__restrict__ rvdw, Geom g, double beta,
+                                                       double r_cut, double damp_cut, double damp_beta, double damp_d,
+                                                       int *__restrict__ ecnt, int *__restrict__ pcnt,
+                                                       int *__restrict__ entries, RealPair<T> *__restrict__ pairs,
+                                                       int *__restrict__ err) {
+    __shared__ unsigned long long key[kClusterSortCap];
+    __shared__ int eidx[kClusterSortCap], slot[kClusterSortCap];
+    __shared__ int at[kClusterSize], rb[kClusterSize + 1], ilstart[kClusterSize];
+    __shared__ int s_total;
+    const int c = blockIdx.x;
+    if (c >= nclus) return;
+    if (threadIdx.x < kClusterSize) {
+        const int idx = c * kClusterSize + threadIdx.x;
+        at[threadIdx.x] = idx < N ? order[idx] : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        rb[0] = 0;
+        for (int l = 0; l < kClusterSize; ++l) rb[l + 1] = rb[l] + (at[l] >= 0 ? row[at[l] + 1] - row[at[l]] : 0);
+        s_total = rb[kClusterSize];
+    }
+    __syncthreads();
+    const int total = s_total;
+    if (total > kClusterSortCap) {                 // the caller falls back to per-atom pairs
+        if (threadIdx.x == 0) {
+            atomicOr(err, 1);
+            if (COUNT) {
+                ecnt[c] = 0;
+                for (int l = 0; l < kClusterSize; ++l) pcnt[c * kClusterSize + l] = 0;
+            }
+        }
+        return;
+    }
+    int n = 1;
+    while (n < total) n <<= 1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        unsigned long long kv = ~0ull;
+        if (k < total) {
+            int l = 0;
+            while (rb[l + 1] <= k) ++l;
+            const int q = row[at[l]] + (k - rb[l]);
+            kv = ((unsigned long long)col[q] << 27) | ((unsigned long long)(shift[q] & 0xffffff) << 3) |
+                 (unsigned long long)l;
+        }
+        key[k] = kv;
+    }
+    __syncthreads();
+    bitonic_sort_smem(key, n);
+    // entry index of every pair (a new entry at each new j) and its slot
+    // among the pairs of its atom (order of the sorted keys)
+    if (threadIdx.x == 0) {   // serial (at most kClusterSortCap pairs; setup only)
+        int ne = 0, cnt[kClusterSize];
+        for (int l = 0; l < kClusterSize; ++l) cnt[l] = 0;
+        for (int k = 0; k < total; ++k) {
+            if (k == 0 || (key[k] >> 27) != (key[k - 1] >> 27)) ++ne;
+            eidx[k] = ne - 1;
+            const int l = (int)(key[k] & 7ull);
+            slot[k] = cnt[l]++;
+        }
+        int acc = 0;
+        for (int l = 0; l < kClusterSize; ++l) {
+            ilstart[l] = acc;
+            acc += cnt[l];
+            if (COUNT) pcnt[c * kClusterSize + l] = cnt[l];
+        }
+        if (COUNT) ecnt[c] = ne;
+    }
+    __syncthreads();
+    if (COUNT) return;
+    const int e0 = ecnt[c], p0 = pcnt[c * kClusterSize];   // scanned starts
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const int il = (int)(key[k] & 7ull), j = (int)(key[k] >> 27), sh = (int)((key[k] >> 3) & 0xffffff);
+        if (k == 0 || eidx[k] != eidx[k - 1]) entries[e0 + eidx[k]] = j;
+        // the pair tensor of atom il and (j, image), FP64 from the positions
+        const int i = at[il];
+        const double n1 = double((sh & 255) - 128), n2 = double(((sh >> 8) & 255) - 128),
+                     n3 = double(((sh >> 16) & 255) - 128);
+        const double rx = pos[3 * i] - pos[3 * j] - (n1 * g.cell[0] + n2 * g.cell[3] + n3 * g.cell[6]);
+        const double ry = pos[3 * i + 1] - pos[3 * j + 1] - (n1 * g.cell[1] + n2 * g.cell[4] + n3 * g.cell[7]);
+        const double rz = pos[3 * i + 2] - pos[3 * j + 2] - (n1 * g.cell[2] + n2 * g.cell[5] + n3 * g.cell[8]);
+        const PairRadial pr = pair_radial(rx * rx + ry * ry + rz * rz, rvdw[i] + rvdw[j], beta, r_cut, damp_cut,
+                                          damp_beta, damp_d);
+        RealPair<T> rp;
+        rp.e = eidx[k];
+        rp.pad = 0;
+        rp.a[0] = T(pr.cid - pr.crr * rx * rx);
+        rp.a[1] = T(-pr.crr * rx * ry);
+        rp.a[2] = T(-pr.crr * rx * rz);
+        rp.a[3] = T(pr.cid - pr.crr * ry * ry);
+        rp.a[4] = T(-pr.crr * ry * rz);
+        rp.a[5] = T(pr.cid - pr.crr * rz * rz);
+        pairs[(size_t)p0 + ilstart[il] + slot[k]] = rp;
+    }
+}
 }  // namespace
+
+// Atoms in the Morton order of their bricks (bins): close atoms are close in
+// the order, in compact groups.  order: [N].  Returns MBD_ERR_UNSUPPORTED when
+// the brick grid is too large for the Morton cube (the caller keeps the
+// brick-major order).
+mbd_status launch_morton_order(const BinView &B, int N, int *order, DevBuf &cnt, DevBuf &start, DevBuf &bsum,
+                               cudaStream_t st) {
+    int M = 1;
+    while (M < B.nb1 || M < B.nb2 || M < B.nb3) M <<= 1;
+    const unsigned long long mtotal = (unsigned long long)M * M * M;
+    if (mtotal > (1ull << 24) || M > 1024) return MBD_ERR_UNSUPPORTED;
+    MBD_TRY(cnt.ensure(sizeof(int) * mtotal));
+    MBD_TRY(start.ensure(sizeof(int) * (mtotal + 1)));
+    const unsigned blocks = (unsigned)((mtotal + 255) / 256);
+    k_morton_count<<<blocks, 256, 0, st>>>((unsigned)mtotal, B, cnt.as<int>());
+    MBD_LAUNCH_CHECK();
+    MBD_TRY(launch_exclusive_scan(cnt.as<int>(), start.as<int>(), (int)mtotal, bsum, st));
+    if (N > 0) {
+        k_morton_fill<<<blocks, 256, 0, st>>>((unsigned)mtotal, B, start.as<int>(), order);
+        MBD_LAUNCH_CHECK();
+    }
+    return MBD_OK;
+}
+
+// The clusters of the real-space field (k_cluster_pairs): counts, scans of
+// the entry starts (per cluster) and pair starts (per cluster atom), then
+// entries and pairs.  err (device int) gets bit 1 when a cluster has more
+// than kClusterSortCap pairs.
+template <class T>
+mbd_status launch_cluster_pairs(mbd_system *s, const int *order, int nclus, DevBuf &ecnt, DevBuf &pcnt,
+                                DevBuf &estart, DevBuf &pstart, DevBuf &entries, DevBuf &A, int *err,
+                                cudaStream_t st) {
+    const Geom g = make_geom(s);
+    const int nslots = nclus * kClusterSize;
+    MBD_TRY(ecnt.ensure(sizeof(int) * std::max(1, nclus)));
+    MBD_TRY(pcnt.ensure(sizeof(int) * std::max(1, nslots)));
+    MBD_TRY(estart.ensure(sizeof(int) * (nclus + 1)));
+    MBD_TRY(pstart.ensure(sizeof(int) * (nslots + 1)));
+    const size_t cap = (size_t)std::max<long long>(1, s->nb_cap);
+    MBD_TRY(entries.ensure(sizeof(int) * cap));
+    MBD_TRY(A.ensure(sizeof(RealPair<T>) * cap));
+    if (nclus == 0) return MBD_OK;
+    k_cluster_pairs<T, true><<<nclus, 256, 0, st>>>(
+        s->N, nclus, order, s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(), s->pos_d.as<double>(),
+        s->rvdw_d.as<double>(), g, s->ewald_beta, s->r_cut, s->damp_cut, s->damp_beta, s->damp_d, ecnt.as<int>(),
+        pcnt.as<int>(), nullptr, (RealPair<T> *)nullptr, err);
+    MBD_LAUNCH_CHECK();
+    MBD_TRY(launch_exclusive_scan(ecnt.as<int>(), estart.as<int>(), nclus, s->scan_bsum, st));
+    MBD_TRY(launch_exclusive_scan(pcnt.as<int>(), pstart.as<int>(), nslots, s->scan_bsum, st));
+    k_cluster_pairs<T, false><<<nclus, 256, 0, st>>>(
+        s->N, nclus, order, s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(), s->pos_d.as<double>(),
+        s->rvdw_d.as<double>(), g, s->ewald_beta, s->r_cut, s->damp_cut, s->damp_beta, s->damp_d,
+        estart.as<int>(), pstart.as<int>(), entries.as<int>(), A.template as<RealPair<T>>(), err);
+    MBD_LAUNCH_CHECK();
+    return MBD_OK;
+}
+template mbd_status launch_cluster_pairs<double>(mbd_system *, const int *, int, DevBuf &, DevBuf &, DevBuf &,
+                                                 DevBuf &, DevBuf &, DevBuf &, int *, cudaStream_t);
+template mbd_status launch_cluster_pairs<float>(mbd_system *, const int *, int, DevBuf &, DevBuf &, DevBuf &,
+                                                DevBuf &, DevBuf &, DevBuf &, int *, cudaStream_t);
 
 mbd_status launch_bin_atoms(int N, const int *top, const BinView &B, int *bin_of, int *cnt, int *start,
                             int *cursor, int *atoms, DevBuf &bsum, cudaStream_t st) {

@@ -227,6 +227,20 @@ template <> struct __align__(16) SpreadRec<double> { double w0, w1, w2; int atom
 //   e0_alpha = C_{0 alpha} M1'(t1) M2(t2) + C_{1 alpha} M1(t1) M2'(t2),
 //   e1_alpha = C_{2 alpha} M1(t1) M2(t2),   C_{beta alpha} = K_beta a*_{beta alpha}.
 // Records are grouped by the mesh point (k1, k2, top3_j) (CSR over points).
+// Clusters of the real-space field: kClusterSize consecutive atoms of the
+// Morton order; a cluster with more than kClusterSortCap pairs in all (more
+// than 256 neighbours per atom on average) sends the system back to the
+// per-atom pair loop of the field kernel.
+constexpr int kClusterSize = 8;
+constexpr int kClusterSortCap = 2048;
+// One real-space pair of a cluster atom: the index of the neighbour entry
+// within the cluster and the pair tensor A (xx xy xz yy yz zz).
+template <class T> struct __align__(16) RealPair {
+    int e;
+    int pad;
+    T a[6];
+};
+
 constexpr int kPencilOrder = 6;   // the spline order the pencil spreading is compiled for
 template <class T> struct __align__(16) PencilRec {
     T e0[3], e1[3];
@@ -244,6 +258,8 @@ template <class T> struct PrecData {
     DevBuf w, dw, d2w;  // [N][3][p]
     DevBuf G;           // [K1K2K3] influence function
     DevBuf tw1, tw2, tw3;   // twiddles [K] complex per dimension
+    DevBuf cA;          // [nnz] RealPair<T>: per (cluster, atom), sorted by entry (real-space clusters)
+    DevBuf ereal;       // [N][3][ld] real-space field of the current dipoles (cluster kernel output)
     DevBuf d;           // dipoles [N][3][ld]
     DevBuf mesh;        // [K1K2K3][ld]
 };
@@ -284,6 +300,11 @@ struct mbd_system {
     int tune_ld = 0, tune_field_apb = 0, tune_fft_w = 0, tune_sf3_w = 0;
     int basis_recompute = 0;    // MBD_BASIS_RECOMPUTE: three basis vectors kept, the forces rerun the recurrence
     cudaStream_t stream;
+    // a second stream on which the real-space cluster kernel of a Lanczos step
+    // runs beside the FFT passes (forked after the spreading, joined before the
+    // field kernel)
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double omega_sum;
     mbd::FFTDim fft[3];
     // host copies
@@ -296,6 +317,13 @@ struct mbd_system {
     mbd::DevBuf w64_d, dw64_d;                      // [N][3][p] FP64 stencil weights (setup)
     mbd::DevBuf bin_start_d, bin_atoms_d, order_d;  // spread bins; field atom order
     mbd::DevBuf bin_of_d, bin_cursor_d;             // [N] brick of each atom, [nbins] fill cursors
+    mbd::DevBuf morton_cnt, morton_start;           // Morton order of the bricks (setup scratch)
+    // real-space clusters: the distinct neighbours j of each cluster (CSR by
+    // cluster) and the pair starts per (cluster, atom) [8 nclus + 1]
+    mbd::DevBuf cl_ecnt, cl_pcnt, cl_estart, cl_pstart, cl_entries, cl_err;
+    int n_clusters = 0;
+    bool real_clusters = false;                     // the clusters of the last geometry were built
+    int real_method = MBD_REAL_AUTO;                // mbd_set_real_space_method
     mbd::DevBuf scan_cnt, scan_bsum;                // count / scan scratch of the geometry setup
     long long nb_cap = 0;   // pairs col_d, shift_d and the pair tensors hold (0: not sized yet)
     mbd::NeighborGrid ngrid{};   // the last neighbour search's grid
@@ -329,6 +357,16 @@ mbd_status launch_neighbors(const NeighborGrid &ng, const double *pos, int *cnt_
                             int *err, bool fill, long long cap, cudaStream_t st);
 mbd_status launch_exclusive_scan(const int *in, int *out, int n, DevBuf &bsum, cudaStream_t st);
 template <class T> mbd_status launch_pair_tensors(mbd_system *s, cudaStream_t st);
+mbd_status launch_morton_order(const BinView &B, int N, int *order, DevBuf &cnt, DevBuf &start, DevBuf &bsum,
+                               cudaStream_t st);
+template <class T>
+mbd_status launch_cluster_pairs(mbd_system *s, const int *order, int nclus, DevBuf &ecnt, DevBuf &pcnt,
+                                DevBuf &estart, DevBuf &pstart, DevBuf &entries, DevBuf &A, int *err,
+                                cudaStream_t st);
+// whether this call's real-space field runs on the clusters (probe width ld)
+bool real_on_clusters(const mbd_system *s, int ld, int real_bytes);
+// E_real = sum over real-space pairs A d_j of the clusters (T [N][3][ld])
+template <class T> mbd_status launch_real_clusters(mbd_system *s, const T *d, T *ereal, int ld, cudaStream_t st);
 template <class T> mbd_status launch_splines(mbd_system *s, cudaStream_t st);
 template <class T> mbd_status launch_influence(mbd_system *s, const double *bmod_host, cudaStream_t st);
 

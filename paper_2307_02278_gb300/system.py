@@ -134,6 +134,11 @@ class MBDSystem:
         code = {"store": 0, "recompute": 1}[mode]
         check(lib().mbd_set_basis_storage(self._handle, code), "mbd_set_basis_storage")
 
+    def set_real_space_method(self, method: str):
+        """mbd_set_real_space_method: "auto", "clusters" or "pairs"."""
+        code = {"auto": 0, "clusters": 1, "pairs": 2}[method]
+        check(lib().mbd_set_real_space_method(self._handle, code), "mbd_set_real_space_method")
+
     _CHOICE_KEYS = ("ld", "field_atoms_per_block", "fft_tile", "spread_tile")
 
     def autotune(self, n_probes: int) -> dict:

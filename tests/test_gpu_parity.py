@@ -306,3 +306,46 @@ def test_df64_eigensolver_option(mbd, precision):
     _, f2 = gdf.energy_forces(8, 20, 5)
     f1, f2 = f1.cpu().numpy(), f2.cpu().numpy()
     assert np.abs(f2 - f1).max() <= 1e-11 * np.abs(f1).max()
+
+
+# ------------------------------------------------------------------ real space on clusters
+@pytest.mark.parametrize("which", ["cubic", "skew", "c1"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_real_space_clusters(mbd, which, precision):
+    """The real-space field evaluated on atom clusters (mbd_set_real_space_method)
+    against the oracle and against the per-atom pair loop: the field's real
+    term, C x and the Lanczos quadratures."""
+    s = {"cubic": _small(), "skew": _skew(), "c1": config(1)}[which]
+    tol = 1e-11 if precision == "fp64" else 2e-6
+    gc = mbd.MBDSystem.from_workload(s, precision=precision)
+    gc.set_real_space_method("clusters")
+    gp = mbd.MBDSystem.from_workload(s, precision=precision)
+    gp.set_real_space_method("pairs")
+    d = np.random.default_rng(11).normal(size=(3, s.n_atoms, 3))
+    real = (real_space_matrix(s, "same_split") @ d.reshape(3, -1).T).T.reshape(d.shape)
+    close(gc.field(_t(d), mbd.MBD_TERM_REAL).cpu().numpy(), real, tol)
+    x = np.random.default_rng(12).normal(size=(5, 3 * s.n_atoms))
+    yc = gc.apply_C(_t(x)).cpu().numpy()
+    close(yc, Operator(s, "spme")(x), tol)
+    close(yc, gp.apply_C(_t(x)).cpu().numpy(), tol)
+    _, dc = gc.lanczos_energy(8, 12, 99, details=True)
+    _, dp = gp.lanczos_energy(8, 12, 99, details=True)
+    np.testing.assert_allclose(dc["q"], dp["q"], rtol=1e-12 if precision == "fp64" else 2e-6)
+
+
+def test_real_space_clusters_overflow_falls_back(mbd):
+    """More than 256 neighbours per atom on average: the clusters are not built,
+    asking for them is refused, and the pair loop gives the oracle's C x."""
+    a, n = 2.6, 9                                       # 729 atoms on a jittered cubic lattice, L = 23.4
+    grid = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3) * a
+    pos = grid + np.random.default_rng(8).normal(scale=0.1, size=grid.shape)
+    base = random_system(8, 10.0, 8)
+    k = grid.shape[0]
+    s = base.with_(cell=np.eye(3) * (n * a), pos=pos, alpha=np.full(k, 4.0), omega=np.full(k, 0.5),
+                   r_vdw=np.full(k, 3.2), mesh=(24, 24, 24), r_cut=11.6, damp_cut=11.6)
+    g = mbd.MBDSystem.from_workload(s)
+    with pytest.raises(mbd.MBDError) as e:
+        g.set_real_space_method("clusters")
+    assert e.value.code == 7
+    x = np.random.default_rng(13).normal(size=(2, 3 * s.n_atoms))
+    close(g.apply_C(_t(x)).cpu().numpy(), Operator(s, "spme")(x), 1e-11)
