@@ -557,8 +557,12 @@ mbd_status lanczos_workspace(mbd_system *s, int R, int m, int rows, int field_nb
     z.m = m;
     z.rows = rows;
     // prologue blocks per probe chunk: one per SM (fewer, fuller blocks keep the
-    // two-level norm reduction short), at least 16 rows each
-    z.nblk = std::max(1, std::min((rows + 15) / 16, std::max(1, s->num_sms)));
+    // two-level norm reduction short), at least 16 rows each; vectors of more
+    // than 2^22 values take two to four per SM, so that enough loads are in
+    // flight to stream them from HBM
+    const long long vals = (long long)rows * probe_ld(R);
+    const int per_sm = vals >= (1LL << 24) ? 4 : (vals >= (1LL << 22) ? 2 : 1);
+    z.nblk = std::max(1, std::min((rows + 15) / 16, per_sm * std::max(1, s->num_sms)));
     const size_t ld = z.ld;
     const int nchunk = (z.ld + 31) / 32;
     const int slots = s->basis_recompute ? std::min(3, m) : m;

@@ -41,18 +41,43 @@ __global__ void __launch_bounds__(256) k_prologue(LanczosView lz, int k, int m, 
         const double *Yk1 = k >= 1 ? lz.Y + lz_slot(lz, k - 1) * stride : nullptr;
         const double *Yk2 = k >= 2 ? lz.Y + lz_slot(lz, k - 2) * stride : nullptr;
         const double nrm0 = sqrt((double)rows);
-        for (int row = blockIdx.x * 8 + ty; row < rows; row += gridDim.x * 8) {
-            const size_t o = (size_t)row * ld + r;
-            double ys;
-            if (k == 0) {
-                ys = rademacher(seed, (uint64_t)r, (uint64_t)row) / nrm0;
-            } else {
-                ys = lz.L[o] - ak1 * Yk1[o];
-                if (k >= 2) ys -= bk2 * Yk2[o];
+        // four rows per iteration, all their loads issued before any use, so
+        // that enough bytes are in flight to stream the FP64 vectors from HBM
+        constexpr int UR = 4;
+        const int rstep = gridDim.x * 8;
+        for (int row0 = blockIdx.x * 8 + ty; row0 < rows; row0 += UR * rstep) {
+            double lv[UR], y1[UR], y2[UR], gv[UR];
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int row = row0 + u * rstep;
+                lv[u] = y1[u] = y2[u] = gv[u] = 0.0;
+                if (row < rows) {
+                    const size_t o = (size_t)row * ld + r;
+                    gv[u] = g[row / 3];
+                    if (k >= 1) {
+                        lv[u] = lz.L[o];
+                        y1[u] = Yk1[o];
+                    }
+                    if (k >= 2) y2[u] = Yk2[o];
+                }
             }
-            Yk[o] = ys;
-            dout[o] = D(g[row / 3] * ys);
-            acc += ys * ys;
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int row = row0 + u * rstep;
+                if (row < rows) {
+                    const size_t o = (size_t)row * ld + r;
+                    double ys;
+                    if (k == 0) {
+                        ys = rademacher(seed, (uint64_t)r, (uint64_t)row) / nrm0;
+                    } else {
+                        ys = lv[u] - ak1 * y1[u];
+                        if (k >= 2) ys -= bk2 * y2[u];
+                    }
+                    Yk[o] = ys;
+                    dout[o] = D(gv[u] * ys);
+                    acc += ys * ys;
+                }
+            }
         }
     }
     __shared__ double red[8][32];
