@@ -68,7 +68,8 @@ def parse_args():
                     help="Lanczos steps m per call instead of the workload's (0: the workload's; small cases "
                          "for ncu captures)")
     ap.add_argument("--other-steps", type=int, default=5,
-                    help="timed steps of each other water box reported beside the bench line (0: none)")
+                    help="timed steps of each other water box and of the 64-box batch reported beside the bench "
+                         "line (0: none)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip mbd_autotune (launch choices by the built-in rules)")
     ap.add_argument("--choices", default="",
@@ -569,6 +570,8 @@ def run_ours(args, world, rank, local):
             for name in OTHER_WORKLOADS:
                 if name != args.workload:
                     others[name] = other_workload(mbd, config(WORKLOADS[name]), args, stream, flush)
+            if world == 1:
+                others["batch64"] = batch_measurement(mbd, args, stream, args.other_steps)
 
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -611,22 +614,18 @@ def run_ours(args, world, rank, local):
     return 0
 
 
-def run_batch(args, world, rank, local):
+def batch_measurement(mbd, args, stream, steps):
     """The uneven 64-box workload: every box's Lanczos energy in one replayed CUDA
-    graph per step, against the same boxes run one after another."""
+    graph per step, against the same boxes run one after another (L2 flushed
+    before each step, CUDA events on the batch's stream)."""
     import numpy as np
     import torch
 
-    from paper_2307_02278_gb300.build import build
-    build()
-    import paper_2307_02278_gb300 as mbd
     from workloads.systems import batch_systems
 
-    torch.cuda.set_device(local)
     systems = batch_systems()
     R, m = systems[0].n_probes, systems[0].n_steps
     seeds = np.array([s.probe_seed for s in systems], dtype=np.uint64)
-    stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     batch = mbd.MBDBatch(systems, precision=args.precision, quadrature=args.quadrature, stream=stream)
     setup_s = time.perf_counter() - t0
@@ -636,12 +635,9 @@ def run_batch(args, world, rank, local):
     for _ in range(max(0, args.warmup - 1)):
         batch.lanczos_energy(R, m, seeds)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
-    sampler = ClockSampler(visible[local] if local < len(visible) else local)
-    time.sleep(0.3)
     torch.cuda.synchronize()
     ms = []
-    for k in range(args.steps):
+    for k in range(steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -650,7 +646,6 @@ def run_batch(args, world, rank, local):
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
-    clocks = sampler.stop()
     info = batch.info()
     batch.close()
     t_step = float(np.mean(ms)) * 1e-3
@@ -662,7 +657,7 @@ def run_batch(args, world, rank, local):
                                            stream=stream) for s in systems]
     for s, g in zip(systems, singles):
         g.lanczos_energy(R, m, s.probe_seed)
-    for k in range(min(args.steps, 3)):
+    for k in range(min(steps, 3)):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -673,24 +668,43 @@ def run_batch(args, world, rank, local):
         seq_ms.append(a.elapsed_time(b))
     for g in singles:
         g.close()
+    del flush
     t_seq = float(np.mean(seq_ms)) * 1e-3
     max_rel = float(np.max(np.abs(np.asarray(e_seq) - energies) / np.abs(energies)))
-    out = {
+    return {
         "metric": "probe-matvecs/s over a batch of uneven systems", "value": n_sys * R * m / t_step,
-        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 operator / f64 lanczos" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "unit": UNIT, "steps": steps, "ms_per_step": t_step * 1e3,
         "config": {"workload": f"batch{n_sys}_random_N200-20000", "n_sys": n_sys, "total_atoms": atoms,
                    "n_atoms": [s.n_atoms for s in systems], "mesh": [s.mesh[0] for s in systems],
                    "n_probes": R, "n_steps": m, "precision": args.precision,
                    "step": "mbd_batch_lanczos_energy (one CUDA graph replay, energies of all boxes)",
                    "l2": "flushed before every timed step (512 MB write, outside the events)"},
         "ns_per_atom_probe_step": t_step * 1e9 / (atoms * R * m),
-        "graph_kernels": info["graph_kernels"], "gpu_launches": info["graph_kernels"],
+        "graph_kernels": info["graph_kernels"],
         "sequential_ms_per_step": t_seq * 1e3, "speedup_over_sequential": t_seq / t_step,
         "max_rel_diff_vs_sequential": max_rel, "setup_s": setup_s, "first_call_with_capture_s": capture_s,
-        "clocks": clocks, "kernel_sources": source_hash(),
     }
+
+
+def run_batch(args, world, rank, local):
+    """--workload batch64: the batch measurement as the JSON line."""
+    import torch
+
+    from paper_2307_02278_gb300.build import build
+    build()
+    import paper_2307_02278_gb300 as mbd
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    sampler = ClockSampler(visible[local] if local < len(visible) else local)
+    time.sleep(0.3)
+    out = batch_measurement(mbd, args, stream, args.steps)
+    clocks = sampler.stop()
+    out.update({"n_gpus": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 operator / f64 lanczos" if args.precision == "mixed" else "f64",
+                "data": "synthetic", "gpu_launches": out["graph_kernels"], "clocks": clocks,
+                "kernel_sources": source_hash()})
     print(json.dumps(out), flush=True)
     return 0
 

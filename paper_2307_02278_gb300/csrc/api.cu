@@ -511,21 +511,6 @@ mbd_status create_impl(const mbd_system_desc *d, void *stream, mbd_system **out)
         return fail(MBD_ERR_OOM);
     }
     cudaError_t ce;
-    // the second stream has the highest priority: the FFT passes' large grids
-    // otherwise hold every SM until their last wave, and the real-space blocks
-    // would run only in that tail
-    int prio_lo = 0, prio_hi = 0;
-    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
-        cudaGetLastError();
-        prio_hi = 0;
-    }
-    if ((ce = cudaStreamCreateWithPriority(&s->stream2, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
-        (ce = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (ce = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
-        set_last_error("second stream", ce);
-        cudaGetLastError();
-        return fail(MBD_ERR_CUDA);
-    }
     if ((ce = cudaMemcpyAsync(s->g_d.ptr, g.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) ||
         (ce = cudaMemcpyAsync(s->w2_d.ptr, w2.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s->stream)) ||
         (ce = cudaMemcpyAsync(s->rvdw_d.ptr, s->rvdw.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
@@ -636,10 +621,7 @@ mbd_status enqueue_steps(mbd_system *s, int R, int m, uint64_t seed, const uint6
     fo.lz = z.v;
     // the fused spread + k3 pass exists for the specialised sizes with whole probe-pair tiles
     const bool fuse3 = spread_fft3_supported(s, z.ld, (int)sizeof(T));
-    // real space on clusters: on the second stream beside the FFT passes,
-    // except while stages are timed (their events live on the system stream)
     const bool real_cl = real_on_clusters(s, z.ld, (int)sizeof(T));
-    const bool overlap = real_cl && !s->prof.timing && s->stream2 != nullptr;
     for (int k = 0; k < m; ++k) {
         MBD_STAGE(s, MBD_STAGE_PROLOGUE, 1,
                   launch_prologue_t(s->stream, z.v, k, m, seed, R, z.ld, rows, s->g_d.as<double>(), P.d.ptr,
@@ -647,21 +629,11 @@ mbd_status enqueue_steps(mbd_system *s, int R, int m, uint64_t seed, const uint6
         MBD_STAGE(s, MBD_STAGE_SPREAD, 1,
                   fuse3 ? launch_spread_fft3<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld)
                         : launch_spread<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld));
-        if (overlap) {
-            MBD_CUDA_TRY(cudaEventRecord(s->ev_fork, s->stream));
-            MBD_CUDA_TRY(cudaStreamWaitEvent(s->stream2, s->ev_fork, 0));
-            MBD_TRY(launch_real_clusters<T>(s, P.d.template as<T>(), P.ereal.template as<T>(), z.ld, s->stream2));
-            prof_end(s, MBD_STAGE_REAL, 1, nullptr);
-            MBD_CUDA_TRY(cudaEventRecord(s->ev_join, s->stream2));
-        }
         MBD_STAGE(s, MBD_STAGE_FFT, fuse3 ? 4 : 5, launch_convolve<T>(s, P.mesh.template as<T>(), z.ld, fuse3));
         fo.k = k;
-        if (overlap) {
-            MBD_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
-        } else if (real_cl) {
+        if (real_cl)
             MBD_STAGE(s, MBD_STAGE_REAL, 1,
                       launch_real_clusters<T>(s, P.d.template as<T>(), P.ereal.template as<T>(), z.ld, s->stream));
-        }
         MBD_STAGE(s, MBD_STAGE_FIELD, 1,
                   launch_field<T>(s, P.d.template as<T>(), P.mesh.template as<T>(), R, z.ld, fo));
         if (k == 0 && v0)
@@ -1104,12 +1076,6 @@ mbd_status mbd_create_system(const mbd_system_desc *desc, void *cuda_stream, mbd
 
 void mbd_destroy_system(mbd_system *sys) {
     if (sys == nullptr) return;
-    if (sys->stream2) {
-        cudaStreamSynchronize(sys->stream2);
-        cudaStreamDestroy(sys->stream2);
-    }
-    if (sys->ev_fork) cudaEventDestroy(sys->ev_fork);
-    if (sys->ev_join) cudaEventDestroy(sys->ev_join);
     if (sys->host_scal) cudaFreeHost(sys->host_scal);
     if (sys->host_status) cudaFreeHost(sys->host_status);
     prof_release(sys);

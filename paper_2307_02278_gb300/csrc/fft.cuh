@@ -4,6 +4,8 @@
 // mesh size, and the spreading fused with the first forward pass.
 #pragma once
 
+#include <algorithm>
+
 #include "mbd_internal.cuh"
 
 namespace mbd {
@@ -20,6 +22,7 @@ template <class T> struct FFTArgs {
     int V;               // complex probe pairs per mesh point (fused pass: G index = e / V)
     int sign;            // -1 forward, +1 inverse (unfused passes)
     int early;           // compile-time passes: programmatic dependent launch (1) or plain (0)
+    int sms;             // multiprocessors (persistent compile-time passes; 0: not persistent)
 };
 
 // Compile-time passes for the smooth sizes listed below (fft_sizes_*.cu).
@@ -377,10 +380,114 @@ __global__ void __launch_bounds__(NT) k_fft_ct(FFTArgs<T> a) {
     }
 }
 
+// 16-byte asynchronous copy from global to shared memory (cp.async, cached
+// in L2 only), and the group fences of those copies.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit16() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait16() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The same pass over whole tiles with persistent blocks: a block takes tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... and, while it transforms one tile
+// (from shared memory, last stage written straight to global memory), the
+// next tile is already arriving in a second shared buffer by asynchronous
+// copies (cp.async, 16 bytes each, issued by all threads).  So the tile loads
+// overlap the arithmetic and the stage barriers of the previous tile instead
+// of stalling every warp of a block on its own load; the arithmetic per
+// element is that of k_fft_ct (bit-identical results).
+// Resident blocks of a persistent pass that its shared memory allows (three
+// tiles and the twiddles), at most three: the register bound that follows.
+template <class T, int K, int W> constexpr int ct_pipe_blocks() {
+    constexpr size_t smem = sizeof(typename Cplx<T>::type) * (3 * (size_t)K * W + K) + 1024;
+    constexpr size_t per = (227u * 1024u) / smem;
+    return per < 1 ? 1 : (per > 3 ? 3 : (int)per);
+}
+
+template <class T, bool FUSED, int K, int W, int NT, int CV, int... RS>
+__global__ void __launch_bounds__(NT, (ct_pipe_blocks<T, K, W>())) k_fft_ct_pipe(FFTArgs<T> a, unsigned ntiles) {
+    using C = typename Cplx<T>::type;
+    static_assert(sizeof...(RS) >= 2, "at least two stages");
+    static_assert((W * sizeof(C)) % 16 == 0, "tile rows of whole 16-byte chunks");
+    constexpr int CPR = (int)(W * sizeof(C) / 16);   // 16-byte chunks per tile row
+    constexpr int EPC = (int)(16 / sizeof(C));       // complex values per chunk
+    extern __shared__ __align__(16) unsigned char smem_cp[];
+    C *in0 = reinterpret_cast<C *>(smem_cp), *in1 = in0 + K * W, *wk = in1 + K * W;
+    C *tw = wk + K * W;
+    pdl_launch_dependents();
+    for (int i = threadIdx.x; i < K; i += NT) tw[i] = a.tw[i];   // set up once per system
+    pdl_wait();
+    const int ncb = a.inner / W;
+    const size_t gstride = (size_t)(a.inner / a.V);
+    unsigned t = blockIdx.x;
+    if (t < ntiles) {
+        const size_t outer = t / ncb;
+        const C *src = a.data + outer * (size_t)K * a.inner + (size_t)(t % ncb) * W;
+        for (int q = threadIdx.x; q < K * CPR; q += NT)
+            cp_async16(in0 + (q / CPR) * W + (q % CPR) * EPC, src + (size_t)(q / CPR) * a.inner + (q % CPR) * EPC);
+    }
+    cp_async_commit16();
+    for (int b = 0; t < ntiles; t += gridDim.x, b ^= 1) {
+        C *cur = b ? in1 : in0, *nxt = b ? in0 : in1;
+        __syncthreads();                         // every thread is done with nxt (two tiles ago) and wk
+        const unsigned tn = t + gridDim.x;
+        if (tn < ntiles) {
+            const size_t outer = tn / ncb;
+            const C *src = a.data + outer * (size_t)K * a.inner + (size_t)(tn % ncb) * W;
+            for (int q = threadIdx.x; q < K * CPR; q += NT)
+                cp_async16(nxt + (q / CPR) * W + (q % CPR) * EPC,
+                           src + (size_t)(q / CPR) * a.inner + (q % CPR) * EPC);
+        }
+        cp_async_commit16();
+        cp_async_wait16<1>();                     // this thread's copies of tile t are done
+        __syncthreads();                         // and every thread's
+        const size_t outer = t / ncb;
+        const int c0 = (int)(t % ncb) * W;
+        C *base = a.data + outer * (size_t)K * a.inner + c0;
+        if (FUSED) {
+            const T *Gb = a.G + outer * (size_t)K * gstride;
+            C *res = ct_pipe<T, C, K, W, NT, CV, 1, false, false, true, RS...>(base, base, a.inner, W, cur, wk, tw,
+                                                                                -1, Gb, gstride, c0, a.V);
+            __syncthreads();
+            C *other = (res == cur) ? wk : cur;
+            ct_pipe<T, C, K, W, NT, CV, 1, false, true, false, RS...>(base, base, a.inner, W, res, other, tw, +1, Gb,
+                                                                       gstride, c0, a.V);
+        } else {
+            ct_pipe<T, C, K, W, NT, CV, 1, false, true, false, RS...>(base, base, a.inner, W, cur, wk, tw, a.sign,
+                                                                       a.G, gstride, c0, a.V);
+        }
+    }
+    cp_async_wait16<0>();                         // no copy in flight at exit
+}
+
 template <class T, bool FUSED, int K, int W, int CV, int... RS> int launch_ct_cv(const FFTArgs<T> &a, unsigned grid,
                                                                               cudaStream_t st) {
     using C = typename Cplx<T>::type;
     constexpr int NT = ct_threads<K, W / CV, RS...>();
+    if (ct_pipe_blocks<T, K, W>() >= 2 && a.inner % W == 0 && a.sms > 0) {
+        // whole tiles and room for two blocks per SM: persistent blocks with the next tile prefetched
+        auto kern = k_fft_ct_pipe<T, FUSED, K, W, NT, CV, RS...>;
+        const size_t smem = sizeof(C) * (3 * (size_t)K * W + K);
+        static int per_sm = -1;                   // resident blocks per SM (one device architecture)
+        if (per_sm < 0) {
+            int x = 0;
+            if (smem > 48 * 1024 &&
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                x = 0;
+            else if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, kern, NT, smem) != cudaSuccess)
+                x = 0;
+            cudaGetLastError();
+            per_sm = x;
+        }
+        if (per_sm > 0) {
+            const unsigned pgrid = (unsigned)std::min<long long>(grid, (long long)per_sm * a.sms);
+            launch_pdl(a.early != 0, kern, dim3(pgrid), dim3(NT), smem, st, a, grid);
+            return 1;
+        }
+    }
     const size_t smem = sizeof(C) * (2 * (size_t)K * W + K);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_fft_ct<T, FUSED, K, W, NT, CV, RS...>, cudaFuncAttributeMaxDynamicSharedMemorySize,

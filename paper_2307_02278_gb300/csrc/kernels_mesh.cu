@@ -998,6 +998,7 @@ template <class T> mbd_status launch_convolve(mbd_system *s, T *mesh, int ld, bo
         a.sign = sign;
         // early launch of the passes while the mesh fits in three quarters of L2
         a.early = npts_bytes <= kEarlyFFTMaxBytes ? 1 : 0;
+        a.sms = s->num_sms;
         // compile-time pass: float tiles of 32 complex columns (16 for narrow
         // rows and for long meshes), double tiles of 16; narrower rows are masked
         FFTArgs<T> c = a;

@@ -300,11 +300,6 @@ struct mbd_system {
     int tune_ld = 0, tune_field_apb = 0, tune_fft_w = 0, tune_sf3_w = 0;
     int basis_recompute = 0;    // MBD_BASIS_RECOMPUTE: three basis vectors kept, the forces rerun the recurrence
     cudaStream_t stream;
-    // a second stream on which the real-space cluster kernel of a Lanczos step
-    // runs beside the FFT passes (forked after the spreading, joined before the
-    // field kernel)
-    cudaStream_t stream2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double omega_sum;
     mbd::FFTDim fft[3];
     // host copies
