@@ -235,7 +235,7 @@ mbd_status mbd_set_basis_storage(mbd_system *sys, int32_t mode);
 /* ---- evaluation of the real-space field (Eq. fld_ewald) ----
  * MBD_REAL_PAIRS: inside the field kernel, each atom's neighbours split over
  *   the warps of a block (every neighbour's dipoles loaded once per pair).
- * MBD_REAL_CLUSTERS: a kernel of its own over clusters of 8 atoms that are
+ * MBD_REAL_CLUSTERS: a kernel of its own over clusters of 16 atoms that are
  *   consecutive in the Morton order of the mesh bricks: a warp loads each
  *   distinct neighbour (j, image) of the cluster once and applies it to every
  *   cluster atom that has it, then the field kernel adds the result.
@@ -243,7 +243,7 @@ mbd_status mbd_set_basis_storage(mbd_system *sys, int32_t mode);
  *   (and probe chunk of 64 FP32 or 32 FP64 probes), else pairs.
  * The two evaluations sum the same pairs in different orders (results agree
  * to rounding).  MBD_ERR_UNSUPPORTED for MBD_REAL_CLUSTERS when a cluster has
- * more than 2048 pairs (more than 256 neighbours per atom on average); the
+ * more than 4096 pairs (more than 256 neighbours per atom on average); the
  * clusters are rebuilt with every geometry. */
 enum { MBD_REAL_AUTO = 0, MBD_REAL_CLUSTERS = 1, MBD_REAL_PAIRS = 2 };
 mbd_status mbd_set_real_space_method(mbd_system *sys, int32_t method);

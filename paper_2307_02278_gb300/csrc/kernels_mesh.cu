@@ -447,15 +447,15 @@ template <class T> struct RealArgs {
     const T *d;          // [N][3][ld]
     T *out;              // [N][3][ld] E_real
     int ld, N, nclus;
-    const int *order;    // cluster c = atoms order[8c .. 8c + 7]
+    const int *order;    // cluster c = atoms order[16c .. 16c + 15]
     const int *estart;   // [nclus + 1] entry starts
-    const int *pstart;   // [8 nclus + 1] pair starts per (cluster, atom)
+    const int *pstart;   // [16 nclus + 1] pair starts per (cluster, atom)
     const int *entries;  // distinct neighbours j of each cluster
     const RealPair<T> *pairs;
 };
 
 // The real-space field E_real = sum over pairs A(r) d_j (Eq. fld_ewald with
-// the damping correction) on clusters: a block per cluster of 8 atoms and
+// the damping correction) on clusters: a block per cluster of 16 atoms and
 // probe chunk (blockIdx.y, 32 PPL probes), warp w for cluster atom w, lanes
 // over PPL consecutive probes.  The block stages the dipoles of the cluster's
 // distinct neighbours in shared memory, kRealCE entries at a time (coalesced
@@ -467,12 +467,15 @@ template <class T> struct RealArgs {
 // (j, image) order: deterministic.
 constexpr int kRealCE = 48;
 template <class T, int PPL>
-__global__ void __launch_bounds__(256) k_real_clusters(RealArgs<T> a) {
+__global__ void __launch_bounds__(32 * kClusterSize) k_real_clusters(RealArgs<T> a) {
     constexpr int NP = 32 * PPL;                   // probes of the block
     constexpr int U = 16 / (int)sizeof(T);         // values per 16-byte load
     constexpr int PER_ROW = NP / U;                // 16-byte loads per staged row
-    __shared__ __align__(16) T sd[kRealCE][3][NP];
-    __shared__ RealPair<T> sp[kClusterSize][32];
+    // dynamic shared memory: the staged dipoles [kRealCE][3][NP], then the
+    // warps' batches of pairs [kClusterSize][32]
+    extern __shared__ __align__(16) unsigned char real_smem[];
+    T(*sd)[3][NP] = reinterpret_cast<T(*)[3][NP]>(real_smem);
+    RealPair<T>(*sp)[32] = reinterpret_cast<RealPair<T>(*)[32]>(real_smem + sizeof(T) * kRealCE * 3 * NP);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x;
     const int pb = blockIdx.y * NP;
@@ -556,16 +559,19 @@ template <class T> struct FieldArgs {
     FieldOut<T> o;
 };
 
-// Field kernel: one block works on `apb` atoms in turn; for each atom its 8
-// warps split the work (warp w takes stencil planes t1 = w, w + 8, ... and
-// neighbours nb0 + w, nb0 + w + 8, ...; warp 0 adds the self term), lanes own
-// VEC consecutive probes.  The 8 partial fields are summed in a fixed order in
+// Field kernel: one block works on `apb` atoms in turn; for each atom its NW
+// warps split the work (warp w takes stencil planes t1 = w, w + NW, ... and,
+// with the pair loop, neighbours nb0 + w, nb0 + w + NW, ...; warp 0 adds the
+// self term, warp NW - 1 the real-space field of the clusters), lanes own VEC
+// consecutive probes.  NW = 8, or NW = p = 6 when the real space comes from
+// the clusters (one warp per stencil plane, none idle).  The 8 partial fields are summed in a fixed order in
 // shared memory and the epilogue selected by o.mode runs with one thread per
 // probe: E* = E^rec + E^dir + E^self (Eqs. ewalddip, spme, fld_ewald,
 // fld_ewald1), l_k = Omega y_k + Diag(g) E*_k and a_k = y_k^T l_k (Eqs. lk3,
 // recurs2).  PC = spline order (0: runtime).
-template <class T, int VEC, int PC>
-__global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC > 0) ? 3 : 2)
+template <class T, int VEC, int PC, int NW>
+__global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T) == 4 && PC > 0) ? 3 : 2)
+                                                        : ((VEC <= 2 && sizeof(T) == 4) ? 4 : 2))
     k_field(FieldArgs<T> a, int apb) {
     constexpr int NLOC = 32 * VEC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -573,12 +579,12 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
     const int r0 = rbase + lane * VEC;
     const bool inld = r0 < a.ld;
     const int p = PC > 0 ? PC : a.g.p;
-    __shared__ T red[kWarps][3][NLOC];
+    __shared__ T red[NW][3][NLOC];
     __shared__ double bsum[NLOC];
-    __shared__ double pcarry[3 * NLOC > kWarps * 32 ? 3 * NLOC - kWarps * 32 : 1];
+    __shared__ double pcarry[3 * NLOC > NW * 32 ? 3 * NLOC - NW * 32 : 1];
     __shared__ double pall[3 * NLOC];
     pdl_launch_dependents();
-    for (int k = threadIdx.x; k < (3 * NLOC > kWarps * 32 ? 3 * NLOC - kWarps * 32 : 1); k += blockDim.x)
+    for (int k = threadIdx.x; k < (3 * NLOC > NW * 32 ? 3 * NLOC - NW * 32 : 1); k += blockDim.x)
         pcarry[k] = 0.0;
     pdl_wait();
     double part = 0.0;                          // y.l of the (component, probe) this thread owns
@@ -597,7 +603,7 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
                 const int top1 = a.sp.top[3 * i], top2 = a.sp.top[3 * i + 1], top3 = a.sp.top[3 * i + 2];
                 const T *w = a.sp.w + (size_t)3 * p * i;
                 const T *dw = a.sp.dw + (size_t)3 * p * i;
-                for (int t1 = warp; t1 < p; t1 += kWarps) {
+                for (int t1 = warp; t1 < p; t1 += NW) {
                     int k1 = top1 - t1;
                     if (k1 < 0) k1 += a.g.K1;
                     const T wa = w[t1], da = dw[t1];
@@ -639,7 +645,7 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
                 }
             }
             if ((a.o.terms & MBD_TERM_REAL) && a.ereal != nullptr) {
-                if (warp == kWarps - 1) {
+                if (warp == NW - 1) {
                     T x[VEC], y[VEC], z[VEC];
                     const T *ei = a.ereal + (size_t)(3 * i) * a.ld + r0;
                     vload<T, VEC>(ei, x);
@@ -655,10 +661,10 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
             } else if (a.o.terms & MBD_TERM_REAL) {
                 const int nb1 = a.pr.row[i + 1];
                 constexpr int B4 = 4;
-                for (int nb = a.pr.row[i] + warp; nb < nb1; nb += B4 * kWarps) {
+                for (int nb = a.pr.row[i] + warp; nb < nb1; nb += B4 * NW) {
                     int jj[B4];
 #pragma unroll
-                    for (int u = 0; u < B4; ++u) jj[u] = (nb + u * kWarps < nb1) ? a.pr.col[nb + u * kWarps] : -1;
+                    for (int u = 0; u < B4; ++u) jj[u] = (nb + u * NW < nb1) ? a.pr.col[nb + u * NW] : -1;
                     T xs[B4][VEC], ys[B4][VEC], zs[B4][VEC];
 #pragma unroll
                     for (int u = 0; u < B4; ++u) {
@@ -672,7 +678,7 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
 #pragma unroll
                     for (int u = 0; u < B4; ++u) {
                         if (jj[u] >= 0) {
-                            const T *A = a.pr.A + 6 * (size_t)(nb + u * kWarps);
+                            const T *A = a.pr.A + 6 * (size_t)(nb + u * NW);
                             const T A0 = A[0], A1 = A[1], A2 = A[2], A3 = A[3], A4 = A[4], A5 = A[5];
 #pragma unroll
                             for (int v = 0; v < VEC; ++v) {
@@ -714,7 +720,7 @@ __global__ void __launch_bounds__(kWarps * 32, (VEC <= 2 && sizeof(T) == 4 && PC
             if (r < a.ld) {
                 T sum = T(0);
 #pragma unroll
-                for (int w = 0; w < kWarps; ++w) sum += red[w][c][t];
+                for (int w = 0; w < NW; ++w) sum += red[w][c][t];
                 const double E = double(sum);
                 const size_t o = (size_t)(3 * i + c) * a.ld + r;
                 if (a.o.mode == kFieldOut) {
@@ -1064,18 +1070,22 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     const int vec = field_vec(ld, (int)sizeof(T));
     const int apb = field_apb(s, ld);
     dim3 grid(field_blocks(s, ld), (ld + 32 * vec - 1) / (32 * vec));
-#define MBD_FIELD_LAUNCH(V, P) k_field<T, V, P><<<grid, kWarps * 32, 0, s->stream>>>(a, apb)
+    const bool six = a.ereal != nullptr && s->p == 6;
+#define MBD_FIELD_LAUNCH(V, P, NW) k_field<T, V, P, NW><<<grid, (NW) * 32, 0, s->stream>>>(a, apb)
     if (vec == 4) {
         if constexpr (sizeof(T) == 4) {
-            if (s->p == 6) MBD_FIELD_LAUNCH(4, 6);
-            else MBD_FIELD_LAUNCH(4, 0);
+            if (six) MBD_FIELD_LAUNCH(4, 6, 6);
+            else if (s->p == 6) MBD_FIELD_LAUNCH(4, 6, kWarps);
+            else MBD_FIELD_LAUNCH(4, 0, kWarps);
         }
     } else if (vec == 2) {
-        if (s->p == 6) MBD_FIELD_LAUNCH(2, 6);
-        else MBD_FIELD_LAUNCH(2, 0);
+        if (six) MBD_FIELD_LAUNCH(2, 6, 6);
+        else if (s->p == 6) MBD_FIELD_LAUNCH(2, 6, kWarps);
+        else MBD_FIELD_LAUNCH(2, 0, kWarps);
     } else {
-        if (s->p == 6) MBD_FIELD_LAUNCH(1, 6);
-        else MBD_FIELD_LAUNCH(1, 0);
+        if (six) MBD_FIELD_LAUNCH(1, 6, 6);
+        else if (s->p == 6) MBD_FIELD_LAUNCH(1, 6, kWarps);
+        else MBD_FIELD_LAUNCH(1, 0, kWarps);
     }
 #undef MBD_FIELD_LAUNCH
     MBD_LAUNCH_CHECK();
@@ -1112,7 +1122,14 @@ template <class T> mbd_status launch_real_clusters(mbd_system *s, const T *d, T 
     if (a.nclus == 0) return MBD_OK;
     constexpr int ppl = sizeof(T) == 4 ? 2 : 1;
     dim3 grid((unsigned)a.nclus, (unsigned)((ld + 32 * ppl - 1) / (32 * ppl)));
-    k_real_clusters<T, ppl><<<grid, 32 * kClusterSize, 0, st>>>(a);
+    const size_t smem = sizeof(T) * kRealCE * 3 * 32 * ppl + sizeof(RealPair<T>) * kClusterSize * 32;
+    static bool attr = false;
+    if (!attr) {
+        MBD_CUDA_TRY(cudaFuncSetAttribute(k_real_clusters<T, ppl>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        attr = true;
+    }
+    k_real_clusters<T, ppl><<<grid, 32 * kClusterSize, smem, st>>>(a);
     MBD_LAUNCH_CHECK();
     return MBD_OK;
 }
@@ -1125,11 +1142,11 @@ int field_vec(int ld, int real_bytes) {
 namespace {
 // Resident blocks per SM of one field-kernel variant (the same on every
 // device of one architecture), asked of the occupancy calculator once.
-template <class T, int V, int P> int field_occupancy() {
+template <class T, int V, int P, int NW = kWarps> int field_occupancy() {
     static int nb = 0;
     if (nb == 0) {
         int x = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, k_field<T, V, P>, kWarps * 32, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, k_field<T, V, P, NW>, NW * 32, 0) != cudaSuccess ||
             x < 1) {
             cudaGetLastError();
             x = 1;
@@ -1141,16 +1158,26 @@ template <class T, int V, int P> int field_occupancy() {
 
 int field_resident_blocks(const mbd_system *s, int ld) {
     const bool p6 = s->p == 6;
+    const bool fp64 = s->precision == MBD_FP64;
+    const bool six = p6 && real_on_clusters(s, ld, fp64 ? 8 : 4);
     int nb;
-    if (s->precision == MBD_FP64) {
+    if (fp64) {
         const int vec = field_vec(ld, 8);
-        nb = vec == 2 ? (p6 ? field_occupancy<double, 2, 6>() : field_occupancy<double, 2, 0>())
-                      : (p6 ? field_occupancy<double, 1, 6>() : field_occupancy<double, 1, 0>());
+        if (six)
+            nb = vec == 2 ? field_occupancy<double, 2, 6, 6>() : field_occupancy<double, 1, 6, 6>();
+        else
+            nb = vec == 2 ? (p6 ? field_occupancy<double, 2, 6>() : field_occupancy<double, 2, 0>())
+                          : (p6 ? field_occupancy<double, 1, 6>() : field_occupancy<double, 1, 0>());
     } else {
         const int vec = field_vec(ld, 4);
-        nb = vec == 4   ? (p6 ? field_occupancy<float, 4, 6>() : field_occupancy<float, 4, 0>())
-             : vec == 2 ? (p6 ? field_occupancy<float, 2, 6>() : field_occupancy<float, 2, 0>())
-                        : (p6 ? field_occupancy<float, 1, 6>() : field_occupancy<float, 1, 0>());
+        if (six)
+            nb = vec == 4   ? field_occupancy<float, 4, 6, 6>()
+                 : vec == 2 ? field_occupancy<float, 2, 6, 6>()
+                            : field_occupancy<float, 1, 6, 6>();
+        else
+            nb = vec == 4   ? (p6 ? field_occupancy<float, 4, 6>() : field_occupancy<float, 4, 0>())
+                 : vec == 2 ? (p6 ? field_occupancy<float, 2, 6>() : field_occupancy<float, 2, 0>())
+                            : (p6 ? field_occupancy<float, 1, 6>() : field_occupancy<float, 1, 0>());
     }
     return nb * std::max(1, s->num_sms);
 }

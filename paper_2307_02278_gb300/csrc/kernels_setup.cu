@@ -425,13 +425,13 @@ __global__ void k_morton_fill(unsigned mtotal, BinView B, const int *__restrict_
 }
 
 // ---------------------------------------------------------------- clusters of the real-space field
-// Cluster c is the atoms order[8c .. 8c + 7] (consecutive in the Morton order
+// Cluster c is the atoms order[16c .. 16c + 15] (consecutive in the Morton order
 // of the bricks, so close in space).  Its entries are the distinct neighbours
 // j of its atoms (over all images), in increasing j; its pairs are grouped by
 // the cluster atom il (pair starts per (c, il)) and, within an atom, ordered
 // by (j, image), each carrying the index of its entry and its pair tensor.
 // A block per cluster sorts the cluster's pairs in shared memory (bitonic,
-// keys (j, image, il)); COUNT = true counts entries and pairs, COUNT = false
+// keys (j, image, il), il in the low 4 bits); COUNT = true counts entries and pairs, COUNT = false
 // writes them at the scanned starts.
 __device__ __forceinline__ void bitonic_sort_smem(unsigned long long *key, int n) {
     for (int k = 2; k <= n; k <<= 1) {
@@ -461,8 +461,10 @@ __global__ void __launch_bounds__(256) k_cluster_pairs(int N, int nclus, const i
                                                        int *__restrict__ ecnt, int *__restrict__ pcnt,
                                                        int *__restrict__ entries, RealPair<T> *__restrict__ pairs,
                                                        int *__restrict__ err) {
-    __shared__ unsigned long long key[kClusterSortCap];
-    __shared__ int eidx[kClusterSortCap], slot[kClusterSortCap];
+    extern __shared__ __align__(16) unsigned char cl_smem[];   // kClusterSortCap keys, entry indices, slots
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(cl_smem);
+    int *eidx = reinterpret_cast<int *>(key + kClusterSortCap);
+    int *slot = eidx + kClusterSortCap;
     __shared__ int at[kClusterSize], rb[kClusterSize + 1], ilstart[kClusterSize];
     __shared__ int s_total;
     const int c = blockIdx.x;
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(256) k_cluster_pairs(int N, int nclus, const i
             int l = 0;
             while (rb[l + 1] <= k) ++l;
             const int q = row[at[l]] + (k - rb[l]);
-            kv = ((unsigned long long)col[q] << 27) | ((unsigned long long)(shift[q] & 0xffffff) << 3) |
+            kv = ((unsigned long long)col[q] << 28) | ((unsigned long long)(shift[q] & 0xffffff) << 4) |
                  (unsigned long long)l;
         }
         key[k] = kv;
@@ -510,9 +512,9 @@ __global__ void __launch_bounds__(256) k_cluster_pairs(int N, int nclus, const i
         int ne = 0, cnt[kClusterSize];
         for (int l = 0; l < kClusterSize; ++l) cnt[l] = 0;
         for (int k = 0; k < total; ++k) {
-            if (k == 0 || (key[k] >> 27) != (key[k - 1] >> 27)) ++ne;
+            if (k == 0 || (key[k] >> 28) != (key[k - 1] >> 28)) ++ne;
             eidx[k] = ne - 1;
-            const int l = (int)(key[k] & 7ull);
+            const int l = (int)(key[k] & 15ull);
             slot[k] = cnt[l]++;
         }
         int acc = 0;
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(256) k_cluster_pairs(int N, int nclus, const i
     if (COUNT) return;
     const int e0 = ecnt[c], p0 = pcnt[c * kClusterSize];   // scanned starts
     for (int k = threadIdx.x; k < total; k += blockDim.x) {
-        const int il = (int)(key[k] & 7ull), j = (int)(key[k] >> 27), sh = (int)((key[k] >> 3) & 0xffffff);
+        const int il = (int)(key[k] & 15ull), j = (int)(key[k] >> 28), sh = (int)((key[k] >> 4) & 0xffffff);
         if (k == 0 || eidx[k] != eidx[k - 1]) entries[e0 + eidx[k]] = j;
         // the pair tensor of atom il and (j, image), FP64 from the positions
         const int i = at[il];
@@ -593,14 +595,17 @@ mbd_status launch_cluster_pairs(mbd_system *s, const int *order, int nclus, DevB
     MBD_TRY(entries.ensure(sizeof(int) * cap));
     MBD_TRY(A.ensure(sizeof(RealPair<T>) * cap));
     if (nclus == 0) return MBD_OK;
-    k_cluster_pairs<T, true><<<nclus, 256, 0, st>>>(
+    const size_t smem = (size_t)kClusterSortCap * (sizeof(unsigned long long) + 2 * sizeof(int));
+    MBD_CUDA_TRY(cudaFuncSetAttribute(k_cluster_pairs<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MBD_CUDA_TRY(cudaFuncSetAttribute(k_cluster_pairs<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_cluster_pairs<T, true><<<nclus, 256, smem, st>>>(
         s->N, nclus, order, s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(), s->pos_d.as<double>(),
         s->rvdw_d.as<double>(), g, s->ewald_beta, s->r_cut, s->damp_cut, s->damp_beta, s->damp_d, ecnt.as<int>(),
         pcnt.as<int>(), nullptr, (RealPair<T> *)nullptr, err);
     MBD_LAUNCH_CHECK();
     MBD_TRY(launch_exclusive_scan(ecnt.as<int>(), estart.as<int>(), nclus, s->scan_bsum, st));
     MBD_TRY(launch_exclusive_scan(pcnt.as<int>(), pstart.as<int>(), nslots, s->scan_bsum, st));
-    k_cluster_pairs<T, false><<<nclus, 256, 0, st>>>(
+    k_cluster_pairs<T, false><<<nclus, 256, smem, st>>>(
         s->N, nclus, order, s->row_d.as<int>(), s->col_d.as<int>(), s->shift_d.as<int>(), s->pos_d.as<double>(),
         s->rvdw_d.as<double>(), g, s->ewald_beta, s->r_cut, s->damp_cut, s->damp_beta, s->damp_d,
         estart.as<int>(), pstart.as<int>(), entries.as<int>(), A.template as<RealPair<T>>(), err);

@@ -231,8 +231,8 @@ template <> struct __align__(16) SpreadRec<double> { double w0, w1, w2; int atom
 // Morton order; a cluster with more than kClusterSortCap pairs in all (more
 // than 256 neighbours per atom on average) sends the system back to the
 // per-atom pair loop of the field kernel.
-constexpr int kClusterSize = 8;
-constexpr int kClusterSortCap = 2048;
+constexpr int kClusterSize = 16;
+constexpr int kClusterSortCap = 4096;
 // One real-space pair of a cluster atom: the index of the neighbour entry
 // within the cluster and the pair tensor A (xx xy xz yy yz zz).
 template <class T> struct __align__(16) RealPair {
