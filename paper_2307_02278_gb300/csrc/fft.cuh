@@ -772,9 +772,12 @@ __global__ void __launch_bounds__(NT) k_spread_pencil_fft3(const T *__restrict__
     while (cur <= last) MBD_SPP_FLUSH_ADVANCE();
 #undef MBD_SPP_FLUSH_ADVANCE
     __syncthreads();
+    // the forward k3 transform of the whole tile; float tiles take column
+    // pairs (one 16-byte access and one twiddle for two columns)
     C *base = mesh + pencil * (size_t)K * V + c0;
-    ct_pipe<T, C, K, W, NT, 1, 1, false, true, false, RS...>(base, base, (size_t)V, W, buf0, buf1, tw, -1,
-                                                              (const T *)nullptr, 0, c0, V);
+    constexpr int CV = sizeof(T) == 4 ? 2 : 1;
+    ct_pipe<T, C, K, W, NT, CV, 1, false, true, false, RS...>(base, base, (size_t)V, W, buf0, buf1, tw, -1,
+                                                               (const T *)nullptr, 0, c0, V);
 }
 
 template <class T, int K, int W, int... RS>
