@@ -461,8 +461,9 @@ template <class T> struct RealArgs {
 // distinct neighbours in shared memory, kRealCE entries at a time (coalesced
 // 16-byte loads by all threads), so each neighbour's dipoles come from L2
 // once per cluster.  Each warp reads its atom's pairs (entry index and
-// tensor) 32 at a time into shared memory, one per lane, and applies those
-// whose entries are staged, accumulating in registers: no global load waits
+// tensor) 32 at a time into shared memory, one per lane, counts by a ballot
+// those whose entries are staged (entries increase along a batch) and applies
+// them with no test per pair, accumulating in registers: no global load waits
 // inside the pair loop.  An atom's field is the sum over its pairs in
 // (j, image) order: deterministic.
 constexpr int kRealCE = 48;
@@ -486,6 +487,7 @@ __global__ void __launch_bounds__(32 * kClusterSize) k_real_clusters(RealArgs<T>
     const int slot = c * kClusterSize + warp;
     const int pe = a.pstart[slot + 1];
     int bbase = a.pstart[slot], bn = 0, bi = 0;    // the warp's batch of pairs [bbase, bbase + bn), next bi
+    int ev = 0x7fffffff;                           // entry of the batch's pair held by this lane
     T E[3][PPL];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -495,7 +497,7 @@ __global__ void __launch_bounds__(32 * kClusterSize) k_real_clusters(RealArgs<T>
         const int ne = min(kRealCE, ee - c0);
         __syncthreads();                           // the previous chunk is consumed
         for (int t = threadIdx.x; t < ne * 3 * PER_ROW; t += blockDim.x) {
-            const int q = t / (3 * PER_ROW), rem = t % (3 * PER_ROW), k = rem / PER_ROW, u = rem % PER_ROW;
+            const int q = t / (3 * PER_ROW), rem = t - q * (3 * PER_ROW), k = rem / PER_ROW, u = rem - k * PER_ROW;
             const T *src = a.d + (size_t)(3 * a.entries[c0 + q] + k) * a.ld + pb + u * U;
             T *dst = &sd[q][k][u * U];
             if (vec && pb + u * U + U <= a.ld) {
@@ -514,26 +516,35 @@ __global__ void __launch_bounds__(32 * kClusterSize) k_real_clusters(RealArgs<T>
                 bn = min(32, pe - bbase);
                 bi = 0;
                 __syncwarp();
-                if (lane < bn) sp[warp][lane] = a.pairs[bbase + lane];
+                if (lane < bn) {
+                    const RealPair<T> r = a.pairs[bbase + lane];
+                    sp[warp][lane] = r;
+                    ev = r.e;
+                } else {
+                    ev = 0x7fffffff;
+                }
                 __syncwarp();
             }
-            const RealPair<T> cur = sp[warp][bi];
-            if (cur.e >= lim) break;
-            ++bi;
-            const int q = cur.e - lo;
-            T x[PPL], y[PPL], z[PPL];
+            // the pairs bi .. bi + cnt - 1 of the batch have their entries staged
+            // (entries increase along the batch)
+            const int cnt = __popc(__ballot_sync(0xffffffffu, lane >= bi && ev < lim));
+            for (int t = 0; t < cnt; ++t) {
+                const RealPair<T> &cur = sp[warp][bi + t];
+                const int q = cur.e - lo;
+                T x[PPL], y[PPL], z[PPL];
+                vload<T, PPL>(&sd[q][0][lane * PPL], x);
+                vload<T, PPL>(&sd[q][1][lane * PPL], y);
+                vload<T, PPL>(&sd[q][2][lane * PPL], z);
+                const T A0 = cur.a[0], A1 = cur.a[1], A2 = cur.a[2], A3 = cur.a[3], A4 = cur.a[4], A5 = cur.a[5];
 #pragma unroll
-            for (int e = 0; e < PPL; ++e) {
-                x[e] = sd[q][0][lane * PPL + e];
-                y[e] = sd[q][1][lane * PPL + e];
-                z[e] = sd[q][2][lane * PPL + e];
+                for (int e = 0; e < PPL; ++e) {
+                    E[0][e] += A0 * x[e] + A1 * y[e] + A2 * z[e];
+                    E[1][e] += A1 * x[e] + A3 * y[e] + A4 * z[e];
+                    E[2][e] += A2 * x[e] + A4 * y[e] + A5 * z[e];
+                }
             }
-#pragma unroll
-            for (int e = 0; e < PPL; ++e) {
-                E[0][e] += cur.a[0] * x[e] + cur.a[1] * y[e] + cur.a[2] * z[e];
-                E[1][e] += cur.a[1] * x[e] + cur.a[3] * y[e] + cur.a[4] * z[e];
-                E[2][e] += cur.a[2] * x[e] + cur.a[4] * y[e] + cur.a[5] * z[e];
-            }
+            bi += cnt;
+            if (bi < bn) break;                    // the next pair waits for a later chunk
         }
     }
     const int idx = c * kClusterSize + warp;
