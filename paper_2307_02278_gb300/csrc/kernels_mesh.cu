@@ -584,13 +584,19 @@ template <class T, int VEC, int PC, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T) == 4 && PC > 0) ? 3 : 2)
                                                         : ((VEC <= 2 && sizeof(T) == 4) ? 4 : 2))
     k_field(FieldArgs<T> a, int apb) {
+    // atoms per iteration: with six warps (no pair loop) and four probes per
+    // lane, two atoms are gathered together, their loads interleaved, sharing
+    // one barrier pair (128 probes: 585 -> 527 us per launch at 128^3); with
+    // fewer probes per lane the registers this takes cost a resident block
+    // (64 probes at 192^3: 1236 -> 1369 us), so one atom at a time
+    constexpr int APT = (NW != kWarps && VEC == 4) ? 2 : 1;
     constexpr int NLOC = 32 * VEC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rbase = blockIdx.y * NLOC;
     const int r0 = rbase + lane * VEC;
     const bool inld = r0 < a.ld;
     const int p = PC > 0 ? PC : a.g.p;
-    __shared__ T red[NW][3][NLOC];
+    __shared__ T red[APT][NW][3][NLOC];
     __shared__ double bsum[NLOC];
     __shared__ double pcarry[3 * NLOC > NW * 32 ? 3 * NLOC - NW * 32 : 1];
     __shared__ double pall[3 * NLOC];
@@ -599,47 +605,82 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
         pcarry[k] = 0.0;
     pdl_wait();
     double part = 0.0;                          // y.l of the (component, probe) this thread owns
-    for (int ai = 0; ai < apb; ++ai) {
-        const int idx = blockIdx.x * apb + ai;
-        if (idx >= a.g.N) break;
-        const int i = a.order[idx];
-        T E0[VEC], E1[VEC], E2[VEC];
+    for (int ai = 0; ai < apb; ai += APT) {
+        int iat[APT];
+        bool val[APT];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) E0[v] = E1[v] = E2[v] = T(0);
+        for (int aa = 0; aa < APT; ++aa) {
+            const int idx = blockIdx.x * apb + ai + aa;
+            val[aa] = ai + aa < apb && idx < a.g.N;
+            iat[aa] = val[aa] ? a.order[idx] : 0;
+        }
+        if (!val[0]) break;
+        T E0[APT][VEC], E1[APT][VEC], E2[APT][VEC];
+#pragma unroll
+        for (int aa = 0; aa < APT; ++aa)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) E0[aa][v] = E1[aa][v] = E2[aa][v] = T(0);
         if (inld) {
             if (a.o.terms & MBD_TERM_RECIP) {
-                T f0[VEC], f1[VEC], f2[VEC];
+                T f0[APT][VEC], f1[APT][VEC], f2[APT][VEC];
+                int top1[APT], top2[APT], top3[APT];
+                const T *w[APT], *dw[APT];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) f0[v] = f1[v] = f2[v] = T(0);
-                const int top1 = a.sp.top[3 * i], top2 = a.sp.top[3 * i + 1], top3 = a.sp.top[3 * i + 2];
-                const T *w = a.sp.w + (size_t)3 * p * i;
-                const T *dw = a.sp.dw + (size_t)3 * p * i;
+                for (int aa = 0; aa < APT; ++aa) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) f0[aa][v] = f1[aa][v] = f2[aa][v] = T(0);
+                    const int i = iat[aa];
+                    top1[aa] = a.sp.top[3 * i];
+                    top2[aa] = a.sp.top[3 * i + 1];
+                    top3[aa] = a.sp.top[3 * i + 2];
+                    w[aa] = a.sp.w + (size_t)3 * p * i;
+                    dw[aa] = a.sp.dw + (size_t)3 * p * i;
+                }
                 for (int t1 = warp; t1 < p; t1 += NW) {
-                    int k1 = top1 - t1;
-                    if (k1 < 0) k1 += a.g.K1;
-                    const T wa = w[t1], da = dw[t1];
+                    int k1[APT];
+                    T wa[APT], da[APT];
+#pragma unroll
+                    for (int aa = 0; aa < APT; ++aa) {
+                        k1[aa] = top1[aa] - t1;
+                        if (k1[aa] < 0) k1[aa] += a.g.K1;
+                        wa[aa] = w[aa][t1];
+                        da[aa] = dw[aa][t1];
+                    }
 #pragma unroll
                     for (int t2 = 0; t2 < (PC > 0 ? PC : kMaxOrder); ++t2) {
                         if (t2 >= p) break;
-                        int k2 = top2 - t2;
-                        if (k2 < 0) k2 += a.g.K2;
-                        const T wb = w[p + t2], db = dw[p + t2];
-                        const T ab = wa * wb, Ab = da * wb, aB = wa * db;
-                        const T *rowp = a.mesh + ((size_t)k1 * a.g.K2 + k2) * a.g.K3 * a.ld + r0;
+                        const T *rowp[APT];
+                        T ab[APT], Ab[APT], aB[APT];
+#pragma unroll
+                        for (int aa = 0; aa < APT; ++aa) {
+                            int k2 = top2[aa] - t2;
+                            if (k2 < 0) k2 += a.g.K2;
+                            const T wb = w[aa][p + t2], db = dw[aa][p + t2];
+                            ab[aa] = wa[aa] * wb;
+                            Ab[aa] = da[aa] * wb;
+                            aB[aa] = wa[aa] * db;
+                            rowp[aa] = a.mesh + ((size_t)k1[aa] * a.g.K2 + k2) * a.g.K3 * a.ld + r0;
+                        }
 #pragma unroll
                         for (int t3 = 0; t3 < (PC > 0 ? PC : kMaxOrder); ++t3) {
                             if (t3 >= p) break;
-                            int k3 = top3 - t3;
-                            if (k3 < 0) k3 += a.g.K3;
-                            T phi[VEC];
-                            vload<T, VEC>(rowp + (size_t)k3 * a.ld, phi);
-                            const T wc = w[2 * p + t3], dc = dw[2 * p + t3];
-                            const T c0 = Ab * wc, c1 = aB * wc, c2 = ab * dc;
+                            T phi[APT][VEC];
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) {
-                                f0[v] += c0 * phi[v];
-                                f1[v] += c1 * phi[v];
-                                f2[v] += c2 * phi[v];
+                            for (int aa = 0; aa < APT; ++aa) {
+                                int k3 = top3[aa] - t3;
+                                if (k3 < 0) k3 += a.g.K3;
+                                vload<T, VEC>(rowp[aa] + (size_t)k3 * a.ld, phi[aa]);
+                            }
+#pragma unroll
+                            for (int aa = 0; aa < APT; ++aa) {
+                                const T wc = w[aa][2 * p + t3], dc = dw[aa][2 * p + t3];
+                                const T c0 = Ab[aa] * wc, c1 = aB[aa] * wc, c2 = ab[aa] * dc;
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) {
+                                    f0[aa][v] += c0 * phi[aa][v];
+                                    f1[aa][v] += c1 * phi[aa][v];
+                                    f2[aa][v] += c2 * phi[aa][v];
+                                }
                             }
                         }
                     }
@@ -649,105 +690,119 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
                 const T m10 = T(a.g.cmat[3]), m11 = T(a.g.cmat[4]), m12 = T(a.g.cmat[5]);
                 const T m20 = T(a.g.cmat[6]), m21 = T(a.g.cmat[7]), m22 = T(a.g.cmat[8]);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    E0[v] += m00 * f0[v] + m10 * f1[v] + m20 * f2[v];
-                    E1[v] += m01 * f0[v] + m11 * f1[v] + m21 * f2[v];
-                    E2[v] += m02 * f0[v] + m12 * f1[v] + m22 * f2[v];
-                }
-            }
-            if ((a.o.terms & MBD_TERM_REAL) && a.ereal != nullptr) {
-                if (warp == NW - 1) {
-                    T x[VEC], y[VEC], z[VEC];
-                    const T *ei = a.ereal + (size_t)(3 * i) * a.ld + r0;
-                    vload<T, VEC>(ei, x);
-                    vload<T, VEC>(ei + a.ld, y);
-                    vload<T, VEC>(ei + 2 * (size_t)a.ld, z);
+                for (int aa = 0; aa < APT; ++aa)
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
-                        E0[v] += x[v];
-                        E1[v] += y[v];
-                        E2[v] += z[v];
+                        E0[aa][v] += m00 * f0[aa][v] + m10 * f1[aa][v] + m20 * f2[aa][v];
+                        E1[aa][v] += m01 * f0[aa][v] + m11 * f1[aa][v] + m21 * f2[aa][v];
+                        E2[aa][v] += m02 * f0[aa][v] + m12 * f1[aa][v] + m22 * f2[aa][v];
                     }
-                }
-            } else if (a.o.terms & MBD_TERM_REAL) {
-                const int nb1 = a.pr.row[i + 1];
-                constexpr int B4 = 4;
-                for (int nb = a.pr.row[i] + warp; nb < nb1; nb += B4 * NW) {
-                    int jj[B4];
+            }
 #pragma unroll
-                    for (int u = 0; u < B4; ++u) jj[u] = (nb + u * NW < nb1) ? a.pr.col[nb + u * NW] : -1;
-                    T xs[B4][VEC], ys[B4][VEC], zs[B4][VEC];
+            for (int aa = 0; aa < APT; ++aa) {
+                if (!val[aa]) continue;
+                const int i = iat[aa];
+                if ((a.o.terms & MBD_TERM_REAL) && a.ereal != nullptr) {
+                    if (warp == NW - 1) {
+                        T x[VEC], y[VEC], z[VEC];
+                        const T *ei = a.ereal + (size_t)(3 * i) * a.ld + r0;
+                        vload<T, VEC>(ei, x);
+                        vload<T, VEC>(ei + a.ld, y);
+                        vload<T, VEC>(ei + 2 * (size_t)a.ld, z);
 #pragma unroll
-                    for (int u = 0; u < B4; ++u) {
-                        if (jj[u] >= 0) {
-                            const T *dj = a.d + (size_t)(3 * jj[u]) * a.ld + r0;
-                            vload<T, VEC>(dj, xs[u]);
-                            vload<T, VEC>(dj + a.ld, ys[u]);
-                            vload<T, VEC>(dj + 2 * (size_t)a.ld, zs[u]);
+                        for (int v = 0; v < VEC; ++v) {
+                            E0[aa][v] += x[v];
+                            E1[aa][v] += y[v];
+                            E2[aa][v] += z[v];
                         }
                     }
+                } else if (a.o.terms & MBD_TERM_REAL) {
+                    const int nb1 = a.pr.row[i + 1];
+                    constexpr int B4 = 4;
+                    for (int nb = a.pr.row[i] + warp; nb < nb1; nb += B4 * NW) {
+                        int jj[B4];
 #pragma unroll
-                    for (int u = 0; u < B4; ++u) {
-                        if (jj[u] >= 0) {
-                            const T *A = a.pr.A + 6 * (size_t)(nb + u * NW);
-                            const T A0 = A[0], A1 = A[1], A2 = A[2], A3 = A[3], A4 = A[4], A5 = A[5];
+                        for (int u = 0; u < B4; ++u) jj[u] = (nb + u * NW < nb1) ? a.pr.col[nb + u * NW] : -1;
+                        T xs[B4][VEC], ys[B4][VEC], zs[B4][VEC];
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) {
-                                E0[v] += A0 * xs[u][v] + A1 * ys[u][v] + A2 * zs[u][v];
-                                E1[v] += A1 * xs[u][v] + A3 * ys[u][v] + A4 * zs[u][v];
-                                E2[v] += A2 * xs[u][v] + A4 * ys[u][v] + A5 * zs[u][v];
+                        for (int u = 0; u < B4; ++u) {
+                            if (jj[u] >= 0) {
+                                const T *dj = a.d + (size_t)(3 * jj[u]) * a.ld + r0;
+                                vload<T, VEC>(dj, xs[u]);
+                                vload<T, VEC>(dj + a.ld, ys[u]);
+                                vload<T, VEC>(dj + 2 * (size_t)a.ld, zs[u]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < B4; ++u) {
+                            if (jj[u] >= 0) {
+                                const T *A = a.pr.A + 6 * (size_t)(nb + u * NW);
+                                const T A0 = A[0], A1 = A[1], A2 = A[2], A3 = A[3], A4 = A[4], A5 = A[5];
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) {
+                                    E0[aa][v] += A0 * xs[u][v] + A1 * ys[u][v] + A2 * zs[u][v];
+                                    E1[aa][v] += A1 * xs[u][v] + A3 * ys[u][v] + A4 * zs[u][v];
+                                    E2[aa][v] += A2 * xs[u][v] + A4 * ys[u][v] + A5 * zs[u][v];
+                                }
                             }
                         }
                     }
                 }
-            }
-            if ((a.o.terms & MBD_TERM_SELF) && warp == 0) {
-                const T c = T(a.self_coef);
-                T x[VEC], y[VEC], z[VEC];
-                const T *di = a.d + (size_t)(3 * i) * a.ld + r0;
-                vload<T, VEC>(di, x);
-                vload<T, VEC>(di + a.ld, y);
-                vload<T, VEC>(di + 2 * (size_t)a.ld, z);
+                if ((a.o.terms & MBD_TERM_SELF) && warp == 0) {
+                    const T c = T(a.self_coef);
+                    T x[VEC], y[VEC], z[VEC];
+                    const T *di = a.d + (size_t)(3 * i) * a.ld + r0;
+                    vload<T, VEC>(di, x);
+                    vload<T, VEC>(di + a.ld, y);
+                    vload<T, VEC>(di + 2 * (size_t)a.ld, z);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    E0[v] += c * x[v];
-                    E1[v] += c * y[v];
-                    E2[v] += c * z[v];
+                    for (int v = 0; v < VEC; ++v) {
+                        E0[aa][v] += c * x[v];
+                        E1[aa][v] += c * y[v];
+                        E2[aa][v] += c * z[v];
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            red[warp][0][lane * VEC + v] = E0[v];
-            red[warp][1][lane * VEC + v] = E1[v];
-            red[warp][2][lane * VEC + v] = E2[v];
-        }
+        for (int aa = 0; aa < APT; ++aa)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                red[aa][warp][0][lane * VEC + v] = E0[aa][v];
+                red[aa][warp][1][lane * VEC + v] = E1[aa][v];
+                red[aa][warp][2][lane * VEC + v] = E2[aa][v];
+            }
         __syncthreads();
         // epilogue: one thread per (component, probe) so that the FP64 work
-        // spreads over 6 warps
-        for (int cp = threadIdx.x; cp < 3 * NLOC; cp += blockDim.x) {
-            const int c = cp / NLOC, t = cp - c * NLOC;
-            const int r = rbase + t;
-            if (r < a.ld) {
-                T sum = T(0);
+        // spreads over the warps; the atoms of the iteration in order
 #pragma unroll
-                for (int w = 0; w < NW; ++w) sum += red[w][c][t];
-                const double E = double(sum);
-                const size_t o = (size_t)(3 * i + c) * a.ld + r;
-                if (a.o.mode == kFieldOut) {
-                    a.o.out[o] = E;
-                } else if (a.o.mode == kFieldApply) {
-                    a.o.out[o] = a.w2[i] * a.o.xin[o] + a.g_at[i] * E;
-                } else {
-                    const double invb = a.o.lz.invb[r];
-                    double *Yk = a.o.lz.Y + lz_slot(a.o.lz, a.o.k) * (size_t)(3 * a.g.N) * a.ld;
-                    const double y = Yk[o] * invb;
-                    const double l = a.w2[i] * y + a.g_at[i] * E * invb;
-                    Yk[o] = y;
-                    a.o.lz.L[o] = l;
-                    if (a.o.lz.W) a.o.lz.W[o] += a.o.lz.coef[(size_t)a.o.k * a.ld + r] * y;
-                    if (cp < (int)blockDim.x) part += y * l;
-                    else pcarry[cp - blockDim.x] += y * l;   // thread cp - blockDim.x owns this slot
+        for (int aa = 0; aa < APT; ++aa) {
+            if (!val[aa]) continue;
+            const int i = iat[aa];
+            for (int cp = threadIdx.x; cp < 3 * NLOC; cp += blockDim.x) {
+                const int c = cp / NLOC, t = cp - c * NLOC;
+                const int r = rbase + t;
+                if (r < a.ld) {
+                    T sum = T(0);
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) sum += red[aa][w][c][t];
+                    const double E = double(sum);
+                    const size_t o = (size_t)(3 * i + c) * a.ld + r;
+                    if (a.o.mode == kFieldOut) {
+                        a.o.out[o] = E;
+                    } else if (a.o.mode == kFieldApply) {
+                        a.o.out[o] = a.w2[i] * a.o.xin[o] + a.g_at[i] * E;
+                    } else {
+                        const double invb = a.o.lz.invb[r];
+                        double *Yk = a.o.lz.Y + lz_slot(a.o.lz, a.o.k) * (size_t)(3 * a.g.N) * a.ld;
+                        const double y = Yk[o] * invb;
+                        const double l = a.w2[i] * y + a.g_at[i] * E * invb;
+                        Yk[o] = y;
+                        a.o.lz.L[o] = l;
+                        if (a.o.lz.W) a.o.lz.W[o] += a.o.lz.coef[(size_t)a.o.k * a.ld + r] * y;
+                        if (cp < (int)blockDim.x) part += y * l;
+                        else pcarry[cp - blockDim.x] += y * l;   // thread cp - blockDim.x owns this slot
+                    }
                 }
             }
         }
