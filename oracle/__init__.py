@@ -17,6 +17,8 @@ Layout (each function cites the passage of arXiv 2307.02278 it follows):
   dense.py     exact energy from a full eigendecomposition (Eq. plasmonic) and its gradient
   forces.py    gradient of the bilinear form p^T T'(R) q, the stochastic force estimator
   replica.py   brute-force spherical replica sum (Eq. replica), used only to pin ewald.py
+  scs.py       self-consistent screening of the polarisabilities (the rsSCS front end the
+               review of the MBD model names and leaves out of the paper's scope), dense
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against closed forms, invariants, brute force or an
