@@ -82,7 +82,11 @@ def parse_args():
     ap.add_argument("--study", default="", choices=["", "delta11"],
                     help="delta11: Delta_11 against the mesh for the 14.2 angstrom water and diamond boxes, "
                          "and the parameters mbd_spme_params chooses (JSON lines)")
+    ap.add_argument("--scs-steps", type=int, default=3,
+                    help="timed calls of the screening front end (mbd_scs_screen) on the workload and on the "
+                         "3000-atom box, with the oracle's screening of the 3000-atom box timed beside it (0: none)")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-child-scs", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -282,6 +286,85 @@ def cpu_baseline(seconds: float, workload: str):
         return json.loads(r.stdout.strip().splitlines()[-1])
     except Exception:
         return {"error": (r.stderr or r.stdout)[-300:]}
+
+
+SCS_FREQ = 23
+SCS_TOL = 1e-10
+
+
+def cpu_scs_child():
+    """The oracle's screening (sparse conjugate gradient, one thread) of the
+    3000-atom box, timed; prints its per-atom results' summary."""
+    import numpy as np
+
+    from oracle import scs as oscs
+    from workloads.systems import config
+
+    s = config(2)
+    t0 = time.perf_counter()
+    out = oscs.scs(s, n_freq=SCS_FREQ, solver="cg")
+    dt = time.perf_counter() - t0
+    print(json.dumps({"seconds": dt, "cores": 1, "workload": s.name, "alpha": out["alpha"].tolist(),
+                      "omega": out["omega"].tolist()}))
+
+
+def scs_measurement(mbd, s, args, stream, flush):
+    """Device time of mbd_scs_screen (mixed) on the workload and on the
+    3000-atom box (CUDA events, L2 flushed before each call), the FP64 path on
+    the 3000-atom box, and the oracle's screening of that box on one core."""
+    import numpy as np
+    import torch
+
+    from workloads.systems import config
+
+    def timed(sys_, steps):
+        sys_.scs_screen(n_freq=SCS_FREQ, tol=SCS_TOL)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = sys_.scs_screen(n_freq=SCS_FREQ, tol=SCS_TOL)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.mean(ms)), r
+
+    out = {"n_freq": SCS_FREQ, "tol": SCS_TOL,
+           "includes": "pair records, T_SR evaluated in each product (FP32), CG to tol on every column, "
+                       "C6/omega/R_vdw, host copies"}
+    g = mbd.MBDSystem.from_workload(s, precision="mixed", stream=stream)
+    ms, r = timed(g, args.scs_steps)
+    out["workload"] = {"name": s.name, "ms_per_call": ms, "iterations": r["iterations"], "residual": r["residual"],
+                       "n_pairs": g.info()["n_pairs"], "mean_alpha_scs_over_alpha": float(np.mean(r["alpha"] / s.alpha))}
+    g.close()
+    s2 = config(2)
+    g = mbd.MBDSystem.from_workload(s2, precision="mixed", stream=stream)
+    ms2, r2 = timed(g, args.scs_steps)
+    g.close()
+    g = mbd.MBDSystem.from_workload(s2, precision="fp64", stream=stream)
+    ms64, r64 = timed(g, 1)
+    g.close()
+    out["water3000"] = {"ms_per_call": ms2, "iterations": r2["iterations"], "fp64_ms_per_call": ms64,
+                        "mixed_vs_fp64_max_rel": float(max(np.max(np.abs(r2[k] - r64[k]) / np.abs(r64[k]))
+                                                           for k in ("alpha", "omega", "r_vdw", "c6")))}
+    if not args.no_cpu_baseline:
+        env = dict(os.environ, **SINGLE_THREAD_ENV)
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child-scs"], capture_output=True,
+                           text=True, env=env, cwd=ROOT)
+        try:
+            o = json.loads(p.stdout.strip().splitlines()[-1])
+            worst = max(float(np.max(np.abs(r2[k] - np.asarray(o[k])) / np.abs(np.asarray(o[k]))))
+                        for k in ("alpha", "omega"))
+            out["water3000"]["oracle"] = {"seconds": o["seconds"], "cores": 1, "kind": "oracle",
+                                          "sample": "the oracle's screening of the 3000-atom box (scipy sparse CG "
+                                                    "per column, FP64), the same n_freq",
+                                          "gpu_speedup": o["seconds"] / (ms2 * 1e-3),
+                                          "gpu_mixed_vs_oracle_max_rel": worst}
+        except Exception:
+            out["water3000"]["oracle"] = {"error": (p.stderr or p.stdout)[-300:]}
+    return out
 
 
 # ---------------------------------------------------------------------------- our arm
@@ -565,6 +648,10 @@ def run_ours(args, world, rank, local):
         if not args.no_cufft:
             cufft = cufft_comparison(mbd, s, args.precision, R, stream)
 
+        scs_line = None
+        if args.scs_steps > 0 and world == 1:
+            scs_line = scs_measurement(mbd, s, args, stream, flush)
+
         others = {}
         if args.other_steps > 0:
             for name in OTHER_WORKLOADS:
@@ -601,6 +688,7 @@ def run_ours(args, world, rank, local):
             "fp64_path": fp64,
             "cpu_baseline": cpu,
             "cufft_comparison": cufft,
+            "scs_screen": scs_line,
             "other_workloads": others,
             "gpu_launches": launches_timed,
             "clocks": clocks,
@@ -657,20 +745,30 @@ def batch_measurement(mbd, args, stream, steps):
                                            stream=stream) for s in systems]
     for s, g in zip(systems, singles):
         g.lanczos_energy(R, m, s.probe_seed)
-    for k in range(min(steps, 3)):
+    member_ms = np.zeros(len(systems))
+    n_seq = min(steps, 3)
+    for k in range(n_seq):
         flush.zero_()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e_seq = [g.lanczos_energy(R, m, s.probe_seed) for s, g in zip(systems, singles)]
-        b.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(systems) + 1)]
+        ev[0].record(stream)
+        e_seq = []
+        for i, (s, g) in enumerate(zip(systems, singles)):
+            e_seq.append(g.lanczos_energy(R, m, s.probe_seed))
+            ev[i + 1].record(stream)
         torch.cuda.synchronize()
-        seq_ms.append(a.elapsed_time(b))
+        seq_ms.append(ev[0].elapsed_time(ev[-1]))
+        member_ms += np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(len(systems))]) / n_seq
     for g in singles:
         g.close()
     del flush
     t_seq = float(np.mean(seq_ms)) * 1e-3
     max_rel = float(np.max(np.abs(np.asarray(e_seq) - energies) / np.abs(energies)))
+    # how many of the largest members, each run alone with the whole GPU, already
+    # take as long as the replay of all of them: the others run in their shadow
+    order = np.argsort(-member_ms)
+    cover = int(np.searchsorted(np.cumsum(member_ms[order]), t_step * 1e3) + 1)
+    cover = min(cover, len(systems))
     return {
         "metric": "probe-matvecs/s over a batch of uneven systems", "value": n_sys * R * m / t_step,
         "unit": UNIT, "steps": steps, "ms_per_step": t_step * 1e3,
@@ -683,6 +781,11 @@ def batch_measurement(mbd, args, stream, steps):
         "graph_kernels": info["graph_kernels"],
         "sequential_ms_per_step": t_seq * 1e3, "speedup_over_sequential": t_seq / t_step,
         "max_rel_diff_vs_sequential": max_rel, "setup_s": setup_s, "first_call_with_capture_s": capture_s,
+        "member_ms_alone": [round(float(x), 3) for x in member_ms],
+        "largest_members_alone_covering_replay": {
+            "members": cover, "their_ms_alone": float(np.sum(member_ms[order[:cover]])),
+            "their_atoms": int(sum(systems[i].n_atoms for i in order[:cover])),
+            "rest_ms_alone": float(np.sum(member_ms[order[cover:]]))},
     }
 
 
@@ -766,6 +869,9 @@ def main():
     if args.cpu_child:
         cpu_baseline_child(args.cpu_seconds, args.workload)
         return 0
+    if args.cpu_child_scs:
+        cpu_scs_child()
+        return 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
     if args.study == "delta11":
@@ -776,6 +882,6 @@ def main():
 
 
 if __name__ == "__main__":
-    if "--cpu-child" in sys.argv or "reference" in sys.argv:
+    if "--cpu-child" in sys.argv or "--cpu-child-scs" in sys.argv or "reference" in sys.argv:
         os.environ.update(SINGLE_THREAD_ENV)     # before NumPy is imported
     sys.exit(main())

@@ -145,6 +145,48 @@ mbd_status mbd_lanczos_energy(mbd_system *sys, int32_t n_probes, int32_t n_steps
 mbd_status mbd_energy_forces(mbd_system *sys, int32_t n_probes, int32_t n_steps, uint64_t seed,
                              double *energy, double *forces_dev);
 
+/* ---- self-consistent screening of the polarisabilities (front end) ----
+ * The paper's review of the MBD model notes that the atomic polarisabilities
+ * can be screened by a Dyson-like equation solved at a set of frequencies, and
+ * keeps that step out of its scope: the SPME-Lanczos algorithm takes screened
+ * and unscreened parameters alike.  This call computes the screened
+ * parameters of the range-separated scheme for the system's atoms, geometry
+ * and damping (beta, d, R_vdw):
+ *   alpha_i(iu) = alpha_i / (1 + (u/omega_i)^2),
+ *   sigma_i(u) = (sqrt(2/pi) alpha_i(iu)/3)^(1/3),
+ *   T_SR_ij(u) = sum'_n (1 - s(|r+n|)) T_GG(r+n; sqrt(sigma_i^2 + sigma_j^2)) over
+ *     |r+n| < damp_cut (the truncation of the damping correction), with
+ *     T_GG(r; w) = grad_i grad_j erf(|r|/w)/|r| and s the Fermi damping,
+ *   (A(u)^-1 + T_SR(u)) X_c = 1_c for c = x, y, z, A = diag(alpha_i(iu)),
+ *   alpha_i^SCS(iu) = (1/3) sum_c X_c[i, c],
+ *   C6_i = (3/pi) int_0^inf alpha_i^SCS(iu)^2 du over n_freq Gauss-Legendre
+ *     nodes t mapped to u = 0.5 (1 + t)/(1 - t) Ha,
+ *   omega_i^SCS = 4 C6_i / (3 alpha_i^SCS(0)^2),
+ *   R_vdw,i^SCS = R_vdw,i (alpha_i^SCS(0) / alpha_i)^(1/3).
+ * The solves are a conjugate-gradient iteration per (direction, frequency)
+ * column with the preconditioner A(u), T_SR in the system's operator precision
+ * (FP32 for MBD_MIXED, FP64 for MBD_FP64) and FP64 vectors; it stops when
+ * every column's residual norm is at most tol sqrt(N) (tol relative to the
+ * right-hand side) or after max_iter steps.  A system with screened
+ * parameters is then made with mbd_create_system; its forces are the gradient
+ * at fixed parameters (the dependence of alpha^SCS on positions is not
+ * included).
+ *   n_freq: 1..31 quadrature nodes; tol > 0; max_iter >= 0 (0: the unscreened
+ *   starting point).
+ *   alpha_out, omega_out, r_vdw_out: host [N] (required); c6_out: host [N] or
+ *   NULL; alpha_iu_out: host [n_freq + 1][N] (static first, then the nodes in
+ *   ascending u) or NULL; iterations, residual: host scalars or NULL
+ *   (iterations taken, largest relative residual at exit).
+ * Device memory for the call (the pair tensors, nnz x 32 x 6 values, and six
+ * N x 288 vectors) is allocated and released inside it.  Errors:
+ * MBD_ERR_INVALID_ARG (arguments), MBD_ERR_NOT_POSITIVE_DEFINITE (a column with
+ * p.(A^-1 + T_SR)p <= 0: the polarisation catastrophe), MBD_ERR_NONFINITE,
+ * MBD_ERR_OOM, MBD_ERR_CUDA; outputs untouched on error.  Not reaching tol is
+ * not an error: check *residual. */
+mbd_status mbd_scs_screen(mbd_system *sys, int32_t n_freq, double tol, int32_t max_iter, double *alpha_out,
+                          double *omega_out, double *r_vdw_out, double *c6_out, double *alpha_iu_out,
+                          int32_t *iterations, double *residual);
+
 /* ---- choice of the Ewald splitting, cutoffs and mesh (host only) ----
  * The paper's convergence study of Delta_11 against the mesh (Numerical
  * results section) finds the SPME error set by the density of mesh points,

@@ -30,9 +30,10 @@ mapped to u = u0 (1 + t) / (1 - t) with u0 = 0.5 Ha.
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 from scipy.special import erf
 
-from .ewald import exact_damp_cutoff, pair_list
+from .ewald import exact_damp_cutoff, pair_list, pair_list_tree
 from .model import fermi_damping
 
 U0 = 0.5
@@ -82,19 +83,30 @@ def gg_tensor(rvec, sigma):
     return c_id[..., None, None] * eye - c_rr[..., None, None] * rvec[..., :, None] * rvec[..., None, :]
 
 
-def sr_matrix(sys, u: float, pairs, damp_cut: float) -> np.ndarray:
-    """Dense 3N x 3N T_SR(u) over the pairs (i, j, r = R_i - R_j - n) with |r| < damp_cut."""
+def sr_sparse(sys, u: float, pairs, damp_cut: float) -> sp.csr_matrix:
+    """T_SR(u) as a sparse 3N x 3N matrix over the pairs (i, j, r = R_i - R_j - n)
+    with |r| < damp_cut (repeated (i, j) entries, from different images, add)."""
     i, j, r = pairs
     n = sys.pos.shape[0]
     sig = gaussian_width(dynamic_polarizability(sys.alpha, sys.omega, u))
     rho = np.linalg.norm(r, axis=1)
     one_minus_f = 1.0 - fermi_damping(rho, sys.r_vdw[i] + sys.r_vdw[j], sys.damp_beta, sys.damp_d)
     t = gg_tensor(r, pair_width(sig[i], sig[j])) * ((rho < damp_cut) * one_minus_f)[:, None, None]
-    m = np.zeros((3 * n, 3 * n))
     rows = 3 * i[:, None, None] + np.arange(3)[None, :, None] + 0 * np.arange(3)[None, None, :]
     cols = 3 * j[:, None, None] + np.arange(3)[None, None, :] + 0 * np.arange(3)[None, :, None]
-    np.add.at(m, (rows.ravel(), cols.ravel()), t.ravel())
-    return m
+    return sp.coo_matrix((t.ravel(), (rows.ravel(), cols.ravel())), shape=(3 * n, 3 * n)).tocsr()
+
+
+def sr_matrix(sys, u: float, pairs, damp_cut: float) -> np.ndarray:
+    """Dense 3N x 3N T_SR(u)."""
+    return sr_sparse(sys, u, pairs, damp_cut).toarray()
+
+
+def _unit_columns(n: int) -> np.ndarray:
+    ones = np.zeros((3 * n, 3))
+    for c in range(3):
+        ones[c::3, c] = 1.0
+    return ones
 
 
 def screened_polarizability(sys, u: float, pairs, damp_cut: float) -> np.ndarray:
@@ -102,24 +114,44 @@ def screened_polarizability(sys, u: float, pairs, damp_cut: float) -> np.ndarray
     n = sys.pos.shape[0]
     a_u = dynamic_polarizability(sys.alpha, sys.omega, u)
     m = sr_matrix(sys, u, pairs, damp_cut) + np.diag(np.repeat(1.0 / a_u, 3))
-    ones = np.zeros((3 * n, 3))
-    for c in range(3):
-        ones[c::3, c] = 1.0
-    x = np.linalg.solve(m, ones)
+    x = np.linalg.solve(m, _unit_columns(n))
     return (x[0::3, 0] + x[1::3, 1] + x[2::3, 2]) / 3.0
 
 
-def scs(sys, n_freq: int = 23, mode: str = "same_split", pairs=None) -> dict:
+def screened_polarizability_cg(sys, u: float, pairs, damp_cut: float, rtol: float = 1e-13) -> np.ndarray:
+    """The same by scipy's conjugate gradient on the sparse matrix (preconditioner
+    A(u)), for systems too large for the dense solve."""
+    from scipy.sparse.linalg import LinearOperator, cg
+    n = sys.pos.shape[0]
+    a3 = np.repeat(dynamic_polarizability(sys.alpha, sys.omega, u), 3)
+    m = sr_sparse(sys, u, pairs, damp_cut) + sp.diags(1.0 / a3)
+    pre = LinearOperator(m.shape, matvec=lambda v: a3 * np.ravel(v))
+    b = _unit_columns(n)
+    out = np.zeros(n)
+    for c in range(3):
+        try:
+            x, info = cg(m, b[:, c], x0=a3 * b[:, c], rtol=rtol, atol=0.0, M=pre, maxiter=2000)
+        except TypeError:                        # scipy before 1.12 names it tol
+            x, info = cg(m, b[:, c], x0=a3 * b[:, c], tol=rtol, atol=0.0, M=pre, maxiter=2000)
+        if info != 0:
+            raise RuntimeError(f"cg did not converge (info {info})")
+        out += x[c::3] / 3.0
+    return out
+
+
+def scs(sys, n_freq: int = 23, mode: str = "same_split", pairs=None, solver: str = "dense") -> dict:
     """Screened static polarisabilities, C6 coefficients, characteristic
     frequencies and vdW radii.  mode "same_split": pairs within sys.damp_cut
     (the library's truncation); "exact": within the radius where 1 - f < 1e-17.
+    solver "dense" (np.linalg.solve) or "cg" (sparse, for larger systems).
     alpha_iu[0] is the static value, alpha_iu[k + 1] the value at node u_k."""
     damp_cut = float(sys.damp_cut) if mode == "same_split" else exact_damp_cutoff(sys)
     if pairs is None:
-        pairs = pair_list(sys.cell, sys.pos, damp_cut)
+        pairs = (pair_list_tree if sys.pos.shape[0] > 2000 else pair_list)(sys.cell, sys.pos, damp_cut)
+    solve = screened_polarizability if solver == "dense" else screened_polarizability_cg
     u, w = frequency_grid(n_freq)
-    a0 = screened_polarizability(sys, 0.0, pairs, damp_cut)
-    a_u = np.array([screened_polarizability(sys, float(uk), pairs, damp_cut) for uk in u])
+    a0 = solve(sys, 0.0, pairs, damp_cut)
+    a_u = np.array([solve(sys, float(uk), pairs, damp_cut) for uk in u])
     c6 = 3.0 / np.pi * np.einsum("k,kn->n", w, a_u ** 2)
     return {"alpha": a0, "omega": 4.0 * c6 / (3.0 * a0 ** 2), "r_vdw": sys.r_vdw * (a0 / sys.alpha) ** (1.0 / 3.0),
             "c6": c6, "alpha_iu": np.vstack([a0[None, :], a_u]), "u": np.concatenate([[0.0], u]), "w": w}

@@ -94,6 +94,7 @@ SIGNATURES = {
     "mbd_apply_C": (c_int, [c_void_p, c_int32, c_void_p, c_void_p]),
     "mbd_lanczos_energy": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, PD, PD, PD]),
     "mbd_energy_forces": (c_int, [c_void_p, c_int32, c_int32, c_uint64, PD, c_void_p]),
+    "mbd_scs_screen": (c_int, [c_void_p, c_int32, c_double, c_int32, PD, PD, PD, PD, PD, POINTER(c_int32), PD]),
     "mbd_set_basis_storage": (c_int, [c_void_p, c_int32]),
     "mbd_autotune": (c_int, [c_void_p, c_int32, POINTER(c_int32)]),
     "mbd_set_launch_choices": (c_int, [c_void_p, POINTER(c_int32)]),

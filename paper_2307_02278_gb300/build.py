@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmbd.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["api.cu", "kernels_setup.cu", "kernels_mesh.cu", "kernels_lanczos.cu", "kernels_forces.cu", "noalloc.cu",
-           "params.cu"] + \
+           "params.cu", "scs.cu"] + \
     [f"fft_sizes_{g}.cu" for g in range(6)]
 HEADERS = [os.path.join(CSRC, h) for h in ("mbd_internal.cuh", "ql.cuh", "df64.cuh", "fft.cuh")] + [os.path.join(INCLUDE, "mbd.h")]
 

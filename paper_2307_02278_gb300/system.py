@@ -208,6 +208,21 @@ class MBDSystem:
               "mbd_energy_forces")
         return e.value, forces
 
+    def scs_screen(self, n_freq: int = 23, tol: float = 1e-10, max_iter: int = 200) -> dict:
+        """Screened alpha, omega, R_vdw and C6 per atom (mbd_scs_screen), with
+        alpha^SCS at every frequency [n_freq + 1, N] (static first), the
+        iterations taken and the largest relative residual."""
+        n = self.n_atoms
+        out = {k: np.zeros(n) for k in ("alpha", "omega", "r_vdw", "c6")}
+        aiu = np.zeros((n_freq + 1, n))
+        it = ctypes.c_int32()
+        res = c_double()
+        check(lib().mbd_scs_screen(self._handle, n_freq, tol, max_iter, _dptr(out["alpha"]), _dptr(out["omega"]),
+                                   _dptr(out["r_vdw"]), _dptr(out["c6"]), _dptr(aiu), byref(it), byref(res)),
+              "mbd_scs_screen")
+        out.update(alpha_iu=aiu, iterations=it.value, residual=res.value)
+        return out
+
 
 class MBDBatch:
     """Independent periodic systems of uneven sizes run together (mbd_create_batch):

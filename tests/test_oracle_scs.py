@@ -168,3 +168,11 @@ def test_screened_radius_follows_the_cube_root_of_the_polarisability():
     s = _periodic_system(seed=13)
     out = scs.scs(s, n_freq=6)
     assert np.allclose(out["r_vdw"] ** 3 / out["alpha"], s.r_vdw ** 3 / s.alpha, rtol=1e-13, atol=0)
+
+
+def test_sparse_cg_solve_matches_the_dense_solve():
+    s = _periodic_system(seed=14, n=8, box=10.0)
+    dense = scs.scs(s, n_freq=5)
+    it = scs.scs(s, n_freq=5, solver="cg")
+    for key in ("alpha", "omega", "c6"):
+        assert np.max(np.abs(it[key] - dense[key]) / np.abs(dense[key])) < 1e-11
