@@ -596,7 +596,10 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
     const int r0 = rbase + lane * VEC;
     const bool inld = r0 < a.ld;
     const int p = PC > 0 ? PC : a.g.p;
-    __shared__ T red[APT][NW][3][NLOC];
+    // partial fields of the warps, double-buffered by atom iteration: the
+    // barrier after one iteration's writes also orders the previous epilogue's
+    // reads before the buffer is written again, so one barrier per iteration
+    __shared__ T red[2][APT][NW][3][NLOC];
     __shared__ double bsum[NLOC];
     __shared__ double pcarry[3 * NLOC > NW * 32 ? 3 * NLOC - NW * 32 : 1];
     __shared__ double pall[3 * NLOC];
@@ -606,6 +609,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
     pdl_wait();
     double part = 0.0;                          // y.l of the (component, probe) this thread owns
     for (int ai = 0; ai < apb; ai += APT) {
+        const int rb = (ai / APT) & 1;
         int iat[APT];
         bool val[APT];
 #pragma unroll
@@ -768,9 +772,9 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
         for (int aa = 0; aa < APT; ++aa)
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                red[aa][warp][0][lane * VEC + v] = E0[aa][v];
-                red[aa][warp][1][lane * VEC + v] = E1[aa][v];
-                red[aa][warp][2][lane * VEC + v] = E2[aa][v];
+                red[rb][aa][warp][0][lane * VEC + v] = E0[aa][v];
+                red[rb][aa][warp][1][lane * VEC + v] = E1[aa][v];
+                red[rb][aa][warp][2][lane * VEC + v] = E2[aa][v];
             }
         __syncthreads();
         // epilogue: one thread per (component, probe) so that the FP64 work
@@ -785,7 +789,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
                 if (r < a.ld) {
                     T sum = T(0);
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) sum += red[aa][w][c][t];
+                    for (int w = 0; w < NW; ++w) sum += red[rb][aa][w][c][t];
                     const double E = double(sum);
                     const size_t o = (size_t)(3 * i + c) * a.ld + r;
                     if (a.o.mode == kFieldOut) {
@@ -806,8 +810,8 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
                 }
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (a.o.mode != kFieldLanczos) return;
     // a_k = y_k^T l_k: per probe, the three components in order, then a
     // deterministic reduction over blocks
