@@ -580,26 +580,33 @@ template <class T> struct FieldArgs {
 // probe: E* = E^rec + E^dir + E^self (Eqs. ewalddip, spme, fld_ewald,
 // fld_ewald1), l_k = Omega y_k + Diag(g) E*_k and a_k = y_k^T l_k (Eqs. lk3,
 // recurs2).  PC = spline order (0: runtime).
-template <class T, int VEC, int PC, int NW>
+template <class T, int VEC, int PC, int NW, int LPA = 32>
 __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T) == 4 && PC > 0) ? 3 : 2)
-                                                        : ((VEC <= 2 && sizeof(T) == 4) ? 4 : 2))
+                                                        : (LPA == 16 ? 3 : ((VEC <= 2 && sizeof(T) == 4) ? 4 : 2)))
     k_field(FieldArgs<T> a, int apb) {
     // atoms per iteration: with six warps (no pair loop) and four probes per
     // lane, two atoms are gathered together, their loads interleaved, sharing
-    // one barrier pair (128 probes: 585 -> 527 us per launch at 128^3); with
+    // one barrier (128 probes: 585 -> 527 us per launch at 128^3); with
     // fewer probes per lane the registers this takes cost a resident block
-    // (64 probes at 192^3: 1236 -> 1369 us), so one atom at a time
-    constexpr int APT = (NW != kWarps && VEC == 4) ? 2 : 1;
-    constexpr int NLOC = 32 * VEC;
+    // (64 probes at 192^3: 1236 -> 1369 us).  LPA = 16 (six warps, 64-probe
+    // chunks, four probes per lane): each half-warp gathers its own atom, so a
+    // warp takes two atoms with one atom's registers per lane.
+    constexpr bool HALF = LPA == 16;
+    static_assert(!HALF || (NW != kWarps && VEC == 4), "half-warp atoms: six warps, four probes per lane");
+    constexpr int AIT = HALF ? 2 : ((NW != kWarps && VEC == 4) ? 2 : 1);   // atoms per iteration
+    constexpr int APT = HALF ? 1 : AIT;                                    // atoms per lane
+    constexpr int NLOC = LPA * VEC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = HALF ? (lane >> 4) : 0;          // the lane's atom of the iteration (half-warp mode)
+    const int lid = HALF ? (lane & 15) : lane;
     const int rbase = blockIdx.y * NLOC;
-    const int r0 = rbase + lane * VEC;
+    const int r0 = rbase + lid * VEC;
     const bool inld = r0 < a.ld;
     const int p = PC > 0 ? PC : a.g.p;
     // partial fields of the warps, double-buffered by atom iteration: the
     // barrier after one iteration's writes also orders the previous epilogue's
     // reads before the buffer is written again, so one barrier per iteration
-    __shared__ T red[2][APT][NW][3][NLOC];
+    __shared__ T red[2][AIT][NW][3][NLOC];
     __shared__ double bsum[NLOC];
     __shared__ double pcarry[3 * NLOC > NW * 32 ? 3 * NLOC - NW * 32 : 1];
     __shared__ double pall[3 * NLOC];
@@ -608,17 +615,20 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
         pcarry[k] = 0.0;
     pdl_wait();
     double part = 0.0;                          // y.l of the (component, probe) this thread owns
-    for (int ai = 0; ai < apb; ai += APT) {
-        const int rb = (ai / APT) & 1;
-        int iat[APT];
-        bool val[APT];
+    for (int ai = 0; ai < apb; ai += AIT) {
+        const int rb = (ai / AIT) & 1;
+        int iat[AIT];
+        bool val[AIT];
 #pragma unroll
-        for (int aa = 0; aa < APT; ++aa) {
+        for (int aa = 0; aa < AIT; ++aa) {
             const int idx = blockIdx.x * apb + ai + aa;
             val[aa] = ai + aa < apb && idx < a.g.N;
             iat[aa] = val[aa] ? a.order[idx] : 0;
         }
         if (!val[0]) break;
+        // the lane's own atom in half-warp mode (a select, not an indexed array)
+        const int my_i = (HALF && sub) ? iat[AIT - 1] : iat[0];
+        const bool my_v = (HALF && sub) ? val[AIT - 1] : val[0];
         T E0[APT][VEC], E1[APT][VEC], E2[APT][VEC];
 #pragma unroll
         for (int aa = 0; aa < APT; ++aa)
@@ -633,7 +643,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
                 for (int aa = 0; aa < APT; ++aa) {
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) f0[aa][v] = f1[aa][v] = f2[aa][v] = T(0);
-                    const int i = iat[aa];
+                    const int i = HALF ? my_i : iat[aa];
                     top1[aa] = a.sp.top[3 * i];
                     top2[aa] = a.sp.top[3 * i + 1];
                     top3[aa] = a.sp.top[3 * i + 2];
@@ -704,8 +714,8 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
             }
 #pragma unroll
             for (int aa = 0; aa < APT; ++aa) {
-                if (!val[aa]) continue;
-                const int i = iat[aa];
+                if (!(HALF ? my_v : val[aa])) continue;
+                const int i = HALF ? my_i : iat[aa];
                 if ((a.o.terms & MBD_TERM_REAL) && a.ereal != nullptr) {
                     if (warp == NW - 1) {
                         T x[VEC], y[VEC], z[VEC];
@@ -720,7 +730,7 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
                             E2[aa][v] += z[v];
                         }
                     }
-                } else if (a.o.terms & MBD_TERM_REAL) {
+                } else if (!HALF && (a.o.terms & MBD_TERM_REAL)) {
                     const int nb1 = a.pr.row[i + 1];
                     constexpr int B4 = 4;
                     for (int nb = a.pr.row[i] + warp; nb < nb1; nb += B4 * NW) {
@@ -772,15 +782,15 @@ __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T
         for (int aa = 0; aa < APT; ++aa)
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                red[rb][aa][warp][0][lane * VEC + v] = E0[aa][v];
-                red[rb][aa][warp][1][lane * VEC + v] = E1[aa][v];
-                red[rb][aa][warp][2][lane * VEC + v] = E2[aa][v];
+                red[rb][HALF ? sub : aa][warp][0][lid * VEC + v] = E0[aa][v];
+                red[rb][HALF ? sub : aa][warp][1][lid * VEC + v] = E1[aa][v];
+                red[rb][HALF ? sub : aa][warp][2][lid * VEC + v] = E2[aa][v];
             }
         __syncthreads();
         // epilogue: one thread per (component, probe) so that the FP64 work
         // spreads over the warps; the atoms of the iteration in order
 #pragma unroll
-        for (int aa = 0; aa < APT; ++aa) {
+        for (int aa = 0; aa < AIT; ++aa) {
             if (!val[aa]) continue;
             const int i = iat[aa];
             for (int cp = threadIdx.x; cp < 3 * NLOC; cp += blockDim.x) {
@@ -1142,6 +1152,15 @@ mbd_status launch_field(mbd_system *s, const T *d, const T *mesh, int R, int ld,
     dim3 grid(field_blocks(s, ld), (ld + 32 * vec - 1) / (32 * vec));
     const bool six = a.ereal != nullptr && s->p == 6;
 #define MBD_FIELD_LAUNCH(V, P, NW) k_field<T, V, P, NW><<<grid, (NW) * 32, 0, s->stream>>>(a, apb)
+    if constexpr (sizeof(T) == 4) {
+        if (six && field_half(ld, 4)) {
+            // 64-probe chunks as with two probes per lane, here four probes per
+            // lane on half-warps, one atom each
+            k_field<T, 4, 6, 6, 16><<<grid, 6 * 32, 0, s->stream>>>(a, apb);
+            MBD_LAUNCH_CHECK();
+            return MBD_OK;
+        }
+    }
     if (vec == 4) {
         if constexpr (sizeof(T) == 4) {
             if (six) MBD_FIELD_LAUNCH(4, 6, 6);
@@ -1209,14 +1228,19 @@ int field_vec(int ld, int real_bytes) {
     return (real_bytes == 4 && ld % 4 == 0 && ld >= 128) ? 4 : ((ld % 2 == 0 && ld >= 64) ? 2 : 1);
 }
 
+// FP32 chunks of 64 probes (two per lane) whose probe count allows 16-byte
+// loads: the six-warp field kernel then gathers one atom per half-warp, four
+// probes per lane (the same chunks).
+bool field_half(int ld, int real_bytes) { return real_bytes == 4 && field_vec(ld, 4) == 2 && ld % 4 == 0; }
+
 namespace {
 // Resident blocks per SM of one field-kernel variant (the same on every
 // device of one architecture), asked of the occupancy calculator once.
-template <class T, int V, int P, int NW = kWarps> int field_occupancy() {
+template <class T, int V, int P, int NW = kWarps, int LPA = 32> int field_occupancy() {
     static int nb = 0;
     if (nb == 0) {
         int x = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, k_field<T, V, P, NW>, NW * 32, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, k_field<T, V, P, NW, LPA>, NW * 32, 0) != cudaSuccess ||
             x < 1) {
             cudaGetLastError();
             x = 1;
@@ -1241,9 +1265,10 @@ int field_resident_blocks(const mbd_system *s, int ld) {
     } else {
         const int vec = field_vec(ld, 4);
         if (six)
-            nb = vec == 4   ? field_occupancy<float, 4, 6, 6>()
-                 : vec == 2 ? field_occupancy<float, 2, 6, 6>()
-                            : field_occupancy<float, 1, 6, 6>();
+            nb = vec == 4            ? field_occupancy<float, 4, 6, 6>()
+                 : field_half(ld, 4) ? field_occupancy<float, 4, 6, 6, 16>()
+                 : vec == 2          ? field_occupancy<float, 2, 6, 6>()
+                                     : field_occupancy<float, 1, 6, 6>();
         else
             nb = vec == 4   ? (p6 ? field_occupancy<float, 4, 6>() : field_occupancy<float, 4, 0>())
                  : vec == 2 ? (p6 ? field_occupancy<float, 2, 6>() : field_occupancy<float, 2, 0>())

@@ -400,6 +400,7 @@ mbd_status launch_probes(uint64_t seed, int first, int R, int dim, double *v, cu
 mbd_status launch_dense_step(const double *c, int dim, const LanczosView &lz, int k, int R, int ld, int nblk,
                              cudaStream_t st);
 int field_vec(int ld, int real_bytes);
+bool field_half(int ld, int real_bytes);
 int field_apb(const mbd_system *s, int ld);
 int field_blocks(const mbd_system *s, int ld);
 

@@ -333,6 +333,25 @@ def test_real_space_clusters(mbd, which, precision):
     np.testing.assert_allclose(dc["q"], dp["q"], rtol=1e-12 if precision == "fp64" else 2e-6)
 
 
+@pytest.mark.parametrize("nvec", [64, 100])
+def test_field_half_warp_atoms(mbd, nvec):
+    """Mixed path with 64 to 127 probes on the clusters: the field kernel takes
+    one atom per half-warp (four probes per lane); a ragged second chunk at
+    100.  Against the oracle and against the pair loop (one atom per warp)."""
+    s = config(1)
+    gc = mbd.MBDSystem.from_workload(s, precision="mixed")
+    gc.set_real_space_method("clusters")
+    gp = mbd.MBDSystem.from_workload(s, precision="mixed")
+    gp.set_real_space_method("pairs")
+    x = np.random.default_rng(13).normal(size=(nvec, 3 * s.n_atoms))
+    yc = gc.apply_C(_t(x)).cpu().numpy()
+    close(yc, Operator(s, "spme")(x), 2e-6)
+    close(yc, gp.apply_C(_t(x)).cpu().numpy(), 2e-6)
+    _, dc = gc.lanczos_energy(nvec, 12, 7, details=True)
+    _, dp = gp.lanczos_energy(nvec, 12, 7, details=True)
+    np.testing.assert_allclose(dc["q"], dp["q"], rtol=2e-6)
+
+
 def test_real_space_clusters_overflow_falls_back(mbd):
     """More than 256 neighbours per atom on average: the clusters are not built,
     asking for them is refused, and the pair loop gives the oracle's C x."""
