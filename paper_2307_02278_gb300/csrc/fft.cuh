@@ -750,11 +750,20 @@ __global__ void __launch_bounds__(NT) k_spread_pencil_fft3(const T *__restrict__
             vload<T, PPL>(dj + ld, y);
             vload<T, PPL>(dj + 2 * (size_t)ld, z);
             T m3[P], n3[P];
-            const T *kw = k3w + (size_t)rc.atom * 16;
+            {
+                // the atom's row of 16 values (M3 at 0.., M3' at 8..), 16-byte loads
+                constexpr int U = 16 / (int)sizeof(T);
+                const T *kw = k3w + (size_t)rc.atom * 16;
+                T row[16];
 #pragma unroll
-            for (int t = 0; t < P; ++t) {
-                m3[t] = kw[t];
-                n3[t] = kw[8 + t];
+                for (int b = 0; b < 16; b += U) {
+                    if (b < P || (b + U > 8 && b < 8 + P)) vload<T, U>(kw + b, row + b);
+                }
+#pragma unroll
+                for (int t = 0; t < P; ++t) {
+                    m3[t] = row[t];
+                    n3[t] = row[8 + t];
+                }
             }
             // complete the rows no record of this top3 or later reaches
             const int tcur = rc.top3 + seg * K;
