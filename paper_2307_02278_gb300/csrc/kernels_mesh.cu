@@ -1282,12 +1282,21 @@ int field_resident_blocks(const mbd_system *s, int ld) {
 // resident-block capacity (blocks per SM x SMs, shared by the probe chunks),
 // with at most 64 atoms per block (more waves beyond that, for balance).
 int field_apb(const mbd_system *s, int ld) {
-    if (s->tune_field_apb > 0 && s->tune_ld == ld) return s->tune_field_apb;
-    const int vec = field_vec(ld, s->precision == MBD_FP64 ? 8 : 4);
-    const int ych = (ld + 32 * vec - 1) / (32 * vec);
-    const long long per_wave = std::max(1, field_resident_blocks(s, ld) / ych);
-    const long long waves = (s->N + 64 * per_wave - 1) / (64 * per_wave);
-    return (int)std::max<long long>(1, (s->N + waves * per_wave - 1) / (waves * per_wave));
+    const int bytes = s->precision == MBD_FP64 ? 8 : 4;
+    const int vec = field_vec(ld, bytes);
+    // the six-warp FP32 kernels take two atoms per iteration: an even count
+    // leaves no half-empty iteration
+    const bool pairs = bytes == 4 && s->p == 6 && real_on_clusters(s, ld, bytes) && (vec == 4 || field_half(ld, bytes));
+    int apb;
+    if (s->tune_field_apb > 0 && s->tune_ld == ld) {
+        apb = s->tune_field_apb;
+    } else {
+        const int ych = (ld + 32 * vec - 1) / (32 * vec);
+        const long long per_wave = std::max(1, field_resident_blocks(s, ld) / ych);
+        const long long waves = (s->N + 64 * per_wave - 1) / (64 * per_wave);
+        apb = (int)std::max<long long>(1, (s->N + waves * per_wave - 1) / (waves * per_wave));
+    }
+    return pairs ? apb + (apb & 1) : apb;
 }
 int field_blocks(const mbd_system *s, int ld) {
     const int apb = field_apb(s, ld);
