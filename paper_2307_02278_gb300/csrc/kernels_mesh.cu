@@ -582,7 +582,7 @@ template <class T> struct FieldArgs {
 // recurs2).  PC = spline order (0: runtime).
 template <class T, int VEC, int PC, int NW, int LPA = 32>
 __global__ void __launch_bounds__(NW * 32, NW == kWarps ? ((VEC <= 2 && sizeof(T) == 4 && PC > 0) ? 3 : 2)
-                                                        : (LPA == 16 ? 3 : ((VEC <= 2 && sizeof(T) == 4) ? 4 : 2)))
+                                                        : (LPA == 16 ? 4 : ((VEC <= 2 && sizeof(T) == 4) ? 4 : 2)))
     k_field(FieldArgs<T> a, int apb) {
     // atoms per iteration: with six warps (no pair loop) and four probes per
     // lane, two atoms are gathered together, their loads interleaved, sharing
