@@ -177,8 +177,9 @@ mbd_status mbd_energy_forces(mbd_system *sys, int32_t n_probes, int32_t n_steps,
  *   NULL; alpha_iu_out: host [n_freq + 1][N] (static first, then the nodes in
  *   ascending u) or NULL; iterations, residual: host scalars or NULL
  *   (iterations taken, largest relative residual at exit).
- * Device memory for the call (the pair tensors, nnz x 32 x 6 values, and six
- * N x 288 vectors) is allocated and released inside it.  Errors:
+ * Device memory for the call (MBD_MIXED: a 16-byte record per neighbour pair,
+ * T_SR evaluated inside every product; MBD_FP64: the pair tensors, nnz x 32 x 6
+ * values; and a few N x 288 FP64 vectors) is allocated and released inside it.  Errors:
  * MBD_ERR_INVALID_ARG (arguments), MBD_ERR_NOT_POSITIVE_DEFINITE (a column with
  * p.(A^-1 + T_SR)p <= 0: the polarisation catastrophe), MBD_ERR_NONFINITE,
  * MBD_ERR_OOM, MBD_ERR_CUDA; outputs untouched on error.  Not reaching tol is
