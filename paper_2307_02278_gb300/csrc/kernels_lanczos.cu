@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(64) k_tridiag(const double *__restrict__ a, co
                     apply_rotations(Z + row * zs, cs + pb * m, sn + pb * m, mm, nrot);
         }
         __syncthreads();
-        if (s_done) break;      // the last sweep was applied in this round
+        if (s_done) break;      // the last sweep was applied in this pass
     }
     // q = sum_k U_1k^2 sqrt(theta_k)
     double part = 0.0;
