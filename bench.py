@@ -702,6 +702,18 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def covering_members(member_ms, replay_ms):
+    """The members sorted by their time alone (largest first) and how many of
+    the largest, run one after another with the whole GPU, already take as
+    long as the replay of all of them (the others run in their shadow)."""
+    import numpy as np
+
+    member_ms = np.asarray(member_ms, dtype=float)
+    order = np.argsort(-member_ms, kind="stable")
+    cover = int(np.searchsorted(np.cumsum(member_ms[order]), replay_ms) + 1)
+    return order, min(cover, len(member_ms))
+
+
 def batch_measurement(mbd, args, stream, steps):
     """The uneven 64-box workload: every box's Lanczos energy in one replayed CUDA
     graph per step, against the same boxes run one after another (L2 flushed
@@ -764,11 +776,7 @@ def batch_measurement(mbd, args, stream, steps):
     del flush
     t_seq = float(np.mean(seq_ms)) * 1e-3
     max_rel = float(np.max(np.abs(np.asarray(e_seq) - energies) / np.abs(energies)))
-    # how many of the largest members, each run alone with the whole GPU, already
-    # take as long as the replay of all of them: the others run in their shadow
-    order = np.argsort(-member_ms)
-    cover = int(np.searchsorted(np.cumsum(member_ms[order]), t_step * 1e3) + 1)
-    cover = min(cover, len(systems))
+    order, cover = covering_members(member_ms, t_step * 1e3)
     return {
         "metric": "probe-matvecs/s over a batch of uneven systems", "value": n_sys * R * m / t_step,
         "unit": UNIT, "steps": steps, "ms_per_step": t_step * 1e3,

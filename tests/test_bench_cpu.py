@@ -71,3 +71,10 @@ def test_roofline_line_labels_its_basis(monkeypatch, tmp_path):
     (tmp_path / "profiles" / "dram_traffic.txt").write_text(f"fft w 2000000000 {cur}\n")
     r = bench.roofline(stages, "fft", 8000.0, "measured", "w", 20, npts_bytes=10 ** 6)
     assert abs(r["frac_dram"] - 0.5) < 1e-12 and not r["mesh_exceeds_l2"]
+
+
+def test_covering_members_of_a_batch_replay():
+    order, k = bench.covering_members([5.0, 40.0, 1.0, 30.0, 2.0], 70.0)
+    assert list(order[:2]) == [1, 3] and k == 2                      # 40 + 30 reach the 70 ms replay
+    assert bench.covering_members([5.0, 40.0, 1.0, 30.0, 2.0], 71.0)[1] == 3
+    assert bench.covering_members([1.0, 1.0], 100.0)[1] == 2          # never more than the members
